@@ -1,0 +1,646 @@
+/*
+ * oracle.c -- plain, slow FP64 CPU restatement of the hot path of
+ * "Interactive Volume Visualization via Multi-Resolution Hash Encoding based
+ * Neural Representation" (Wu, Bauer, Doyle, Ma; arXiv 2207.11620).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py load this library.  The GPU
+ * library never links, includes or calls it; the two share no code.
+ *
+ * Precision.  Everything is FP64, except where a floating-point value decides
+ * an integer: the grid cell of a point at a hash level (A-1: p = fl32(x*N_l)),
+ * the voxel cell of a trilinear lookup, the macrocell of a ray sample, the
+ * ray sample positions themselves and the transfer-function index range of a
+ * macrocell.  There the kernel's FP32 operations are restated one by one (this
+ * file is compiled with -ffp-contract=off, so no multiply-add is fused) and
+ * the integer decision is taken on the FP32 value; all arithmetic that
+ * follows the decision is FP64.
+ *
+ * Pins: every function below is checked in tests/test_oracle.py against
+ * values the paper prints, closed forms, brute force or finite differences.
+ * Nothing here is "parity unpinned".
+ *
+ * Data layouts (shared with the GPU path by specification only):
+ *   tables  [L][T][F]            T = 2^log2T, entry (l, h) holds F features
+ *   weights W_0, W_1, ...        W_k is [dims[k+1]][dims[k]] row-major, no bias
+ *   params  = tables followed by weights, one flat vector
+ *   points  [n][3] float32 in [0,1)^3
+ *   volume  [nz][ny][nx] float32, x fastest, cell-centred voxels
+ *   lut     [256][4] float32 RGBA
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Spatial-hash primes of the multi-resolution hash encoding the paper adopts
+ * (Sec. 3.1, which cites instant-NGP for the encoding). */
+#define OR_PI1 1u
+#define OR_PI2 2654435761u
+#define OR_PI3 805459861u
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+/* Sec. 3.1 / Fig. 1B: resolution of level l, N_l = floor(Nmin * b^l), FP64. */
+void or_level_res(int L, int Nmin, double b, int *res) {
+  for (int l = 0; l < L; ++l) res[l] = (int)floor((double)Nmin * pow(b, (double)l));
+}
+
+/* Sec. 3.1: spatial hash of an integer grid vertex into a table of T entries:
+ * XOR of the per-axis products with the primes (1, 2654435761, 805459861) in
+ * uint32 wrap-around arithmetic, reduced mod T. */
+uint32_t or_hash(int64_t vx, int64_t vy, int64_t vz, uint32_t T) {
+  uint32_t h = ((uint32_t)vx * OR_PI1) ^ ((uint32_t)vy * OR_PI2) ^ ((uint32_t)vz * OR_PI3);
+  return h % T;
+}
+
+/* Number of parameters of a network as the paper counts them (App. B, table of
+ * parameter counts): coarse levels stored densely with N_l^3 entries when that
+ * is smaller than T, no biases, output layer padded to out_pad rows. */
+int64_t or_param_count_dense_coarse(int L, int F, int log2T, int base, double scale,
+                                    int n_neurons, int n_hidden, int out_pad) {
+  int64_t T = (int64_t)1 << log2T, total = 0;
+  for (int l = 0; l < L; ++l) {
+    int64_t N = (int64_t)floor((double)base * pow(scale, (double)l));
+    int64_t dense = N * N * N;
+    total += (dense < T ? dense : T) * F;
+  }
+  total += (int64_t)L * F * n_neurons;
+  total += (int64_t)(n_hidden - 1) * n_neurons * n_neurons;
+  total += (int64_t)n_neurons * out_pad;
+  return total;
+}
+
+/* ---------------------------------------------------------------- encode -- */
+
+/* A-1: scale and cell of one coordinate at resolution N.  The product is the
+ * kernel's single FP32 multiply; the cell and the weight follow from it. */
+static void or_cell(float x, int N, int64_t *c, double *w) {
+  float p = x * (float)N;
+  double fl = floor((double)p);
+  *c = (int64_t)fl;
+  *w = (double)p - fl;
+}
+
+/* A-2: the 8 corner indices of point x at level l (corner d = dx + 2dy + 4dz). */
+void or_hash_indices(int L, int log2T, const int *res, const float *xyz, int64_t n, uint32_t *idx) {
+  uint32_t T = 1u << log2T;
+  for (int64_t i = 0; i < n; ++i)
+    for (int l = 0; l < L; ++l) {
+      int64_t c[3]; double w[3];
+      for (int a = 0; a < 3; ++a) or_cell(xyz[3 * i + a], res[l], &c[a], &w[a]);
+      for (int d = 0; d < 8; ++d)
+        idx[(i * L + l) * 8 + d] = or_hash(c[0] + (d & 1), c[1] + ((d >> 1) & 1), c[2] + ((d >> 2) & 1), T);
+    }
+}
+
+/* A-1..A-3 for one point: f[l*F + j] = sum over the 8 corners of the trilinear
+ * weight times table entry j (Sec. 3.1, Fig. 1B: interpolate per level,
+ * concatenate levels). */
+static void or_encode_point(int L, int F, int log2T, const int *res, const double *tables,
+                            const float *x, double *f) {
+  uint32_t T = 1u << log2T;
+  for (int l = 0; l < L; ++l) {
+    int64_t c[3]; double w[3];
+    for (int a = 0; a < 3; ++a) or_cell(x[a], res[l], &c[a], &w[a]);
+    for (int j = 0; j < F; ++j) f[l * F + j] = 0.0;
+    for (int d = 0; d < 8; ++d) {
+      int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+      double wt = (dx ? w[0] : 1.0 - w[0]) * (dy ? w[1] : 1.0 - w[1]) * (dz ? w[2] : 1.0 - w[2]);
+      uint32_t h = or_hash(c[0] + dx, c[1] + dy, c[2] + dz, T);
+      const double *e = tables + ((int64_t)l * T + h) * F;
+      for (int j = 0; j < F; ++j) f[l * F + j] += wt * e[j];
+    }
+  }
+}
+
+void or_encode(int L, int F, int log2T, const int *res, const double *tables,
+               const float *xyz, int64_t n, double *feat) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    or_encode_point(L, F, log2T, res, tables, xyz + 3 * i, feat + i * (int64_t)L * F);
+}
+
+/* ------------------------------------------------------------------- MLP -- */
+
+static double or_sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+static int or_max_dim(const int *dims, int n_dims) {
+  int m = 0;
+  for (int k = 0; k < n_dims; ++k) if (dims[k] > m) m = dims[k];
+  return m;
+}
+
+/* A-4 for one point: a_0 = f; z_{k+1} = W_k a_k; a_{k+1} = ReLU(z_{k+1}) on the
+ * hidden layers; y = sigmoid(z_last) (Sec. 3.1: ReLU on all hidden layers, no
+ * biases; the sigmoid output is the reading stated in the design notes).
+ * act holds every layer's activations back to back (dims[0] + dims[1] + ...)
+ * so the backward pass can reuse them. */
+static double or_mlp_point(const int *dims, int n_dims, const double *weights, double *act) {
+  const double *W = weights;
+  double *a = act;
+  double z_out = 0.0;
+  for (int k = 0; k + 1 < n_dims; ++k) {
+    int din = dims[k], dout = dims[k + 1];
+    double *an = a + din;
+    for (int j = 0; j < dout; ++j) {
+      double z = 0.0;
+      for (int i = 0; i < din; ++i) z += W[(int64_t)j * din + i] * a[i];
+      if (k + 2 < n_dims) an[j] = z > 0.0 ? z : 0.0;
+      else { an[j] = z; z_out = z; }
+    }
+    W += (int64_t)din * dout;
+    a = an;
+  }
+  return or_sigmoid(z_out);
+}
+
+static int64_t or_weight_count(const int *dims, int n_dims) {
+  int64_t c = 0;
+  for (int k = 0; k + 1 < n_dims; ++k) c += (int64_t)dims[k] * dims[k + 1];
+  return c;
+}
+
+static int or_act_len(const int *dims, int n_dims) {
+  int s = 0;
+  for (int k = 0; k < n_dims; ++k) s += dims[k];
+  return s;
+}
+
+/* MLP alone on given inputs (used to pin the MLP separately from the encoding). */
+void or_mlp_forward(const int *dims, int n_dims, const double *weights, const double *in,
+                    int64_t n, double *y) {
+  int alen = or_act_len(dims, n_dims);
+#pragma omp parallel
+  {
+    double *act = (double *)malloc(sizeof(double) * alen);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      memcpy(act, in + i * dims[0], sizeof(double) * dims[0]);
+      y[i] = or_mlp_point(dims, n_dims, weights, act);
+    }
+    free(act);
+  }
+}
+
+/* Encode + MLP: the network value at each point (A-1..A-4). */
+void or_forward(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
+                const double *params, const float *xyz, int64_t n, double *y) {
+  int64_t T = (int64_t)1 << log2T;
+  const double *weights = params + (int64_t)L * T * F;
+  int alen = or_act_len(dims, n_dims);
+#pragma omp parallel
+  {
+    double *act = (double *)malloc(sizeof(double) * alen);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      or_encode_point(L, F, log2T, res, params, xyz + 3 * i, act);
+      y[i] = or_mlp_point(dims, n_dims, weights, act);
+    }
+    free(act);
+  }
+}
+
+/* A-5: L2 loss, the mean over the batch of (y - t)^2 (Sec. 7 names L2 for the
+ * stability-critical case; the batch mean is the reading stated in the design
+ * notes). */
+double or_loss_l2(const double *y, const float *t, int64_t n) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) { double d = y[i] - (double)t[i]; s += d * d; }
+  return n > 0 ? s / (double)n : 0.0;
+}
+
+/* A-6 / A-7: analytic backward of encode + MLP for upstream gradients dL/dy.
+ * Accumulates (+=) into grads, laid out like params (tables then weights).
+ * Chain rule: dz_out = dL/dy * y (1 - y); dW_k += delta_k a_k^T;
+ * delta_{k-1} = (W_k^T delta_k) * 1[z > 0]; df = W_0^T delta_0; the table
+ * gradient of every corner gets its trilinear weight times df (the adjoint of
+ * A-3).  Serial: the scatter into shared table entries is order dependent. */
+void or_backward(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
+                 const double *params, const float *xyz, int64_t n, const double *dL_dy,
+                 double *grads) {
+  uint32_t T = 1u << log2T;
+  int64_t tab = (int64_t)L * T * F;
+  const double *weights = params + tab;
+  double *gw = grads + tab;
+  int alen = or_act_len(dims, n_dims);
+  int mx = or_max_dim(dims, n_dims);
+  double *act = (double *)malloc(sizeof(double) * alen);
+  double *delta = (double *)malloc(sizeof(double) * mx);
+  double *din = (double *)malloc(sizeof(double) * mx);
+  int nl = n_dims - 1;
+  for (int64_t i = 0; i < n; ++i) {
+    const float *x = xyz + 3 * i;
+    or_encode_point(L, F, log2T, res, params, x, act);
+    double y = or_mlp_point(dims, n_dims, weights, act);
+    delta[0] = dL_dy[i] * y * (1.0 - y);
+    /* walk the layers from the output back to the input */
+    for (int k = nl - 1; k >= 0; --k) {
+      int ind = dims[k], outd = dims[k + 1];
+      int64_t woff = 0, aoff = 0;
+      for (int q = 0; q < k; ++q) { woff += (int64_t)dims[q] * dims[q + 1]; aoff += dims[q]; }
+      const double *Wk = weights + woff;
+      const double *ak = act + aoff;
+      double *gWk = gw + woff;
+      for (int j = 0; j < outd; ++j)
+        for (int c = 0; c < ind; ++c) gWk[(int64_t)j * ind + c] += delta[j] * ak[c];
+      for (int c = 0; c < ind; ++c) {
+        double s = 0.0;
+        for (int j = 0; j < outd; ++j) s += Wk[(int64_t)j * ind + c] * delta[j];
+        /* a_k = ReLU(z_k) for k > 0, so 1[z_k > 0] == 1[a_k > 0] */
+        din[c] = (k > 0) ? (ak[c] > 0.0 ? s : 0.0) : s;
+      }
+      memcpy(delta, din, sizeof(double) * ind);
+    }
+    /* delta now holds df (length L*F): scatter into the table gradients */
+    for (int l = 0; l < L; ++l) {
+      int64_t c[3]; double w[3];
+      for (int a = 0; a < 3; ++a) or_cell(x[a], res[l], &c[a], &w[a]);
+      for (int d = 0; d < 8; ++d) {
+        int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+        double wt = (dx ? w[0] : 1.0 - w[0]) * (dy ? w[1] : 1.0 - w[1]) * (dz ? w[2] : 1.0 - w[2]);
+        uint32_t h = or_hash(c[0] + dx, c[1] + dy, c[2] + dz, T);
+        double *g = grads + ((int64_t)l * T + h) * F;
+        for (int j = 0; j < F; ++j) g[j] += wt * delta[l * F + j];
+      }
+    }
+  }
+  free(act); free(delta); free(din);
+}
+
+/* A-8: textbook Adam (Kingma & Ba), as the paper's optimizer (Sec. 3.1, App. B),
+ * dense over every parameter, bias-corrected, step t counted from 1.  l2 is the
+ * weight-decay term added to the gradient before the moments. */
+void or_adam(double *p, const double *g, double *m, double *v, int64_t n, int t,
+             double lr, double b1, double b2, double eps, double l2) {
+  double bc1 = 1.0 - pow(b1, (double)t), bc2 = 1.0 - pow(b2, (double)t);
+  for (int64_t i = 0; i < n; ++i) {
+    double gi = g[i] + l2 * p[i];
+    m[i] = b1 * m[i] + (1.0 - b1) * gi;
+    v[i] = b2 * v[i] + (1.0 - b2) * gi * gi;
+    double mh = m[i] / bc1, vh = v[i] / bc2;
+    p[i] -= lr * mh / (sqrt(vh) + eps);
+  }
+}
+
+/* One training step (Sec. 4): forward on the batch, L2 loss, backward with
+ * dL/dy = 2 (y - t) / n, Adam.  grads is scratch of the params' size and is
+ * left holding this step's gradient.  Returns the loss before the update. */
+double or_train_step(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
+                     double *params, double *grads, double *m, double *v, int64_t n_params,
+                     const float *xyz, const float *target, int64_t n, int t,
+                     double lr, double b1, double b2, double eps, double l2) {
+  double *y = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double *dy = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  or_forward(L, F, log2T, res, dims, n_dims, params, xyz, n, y);
+  double loss = or_loss_l2(y, target, n);
+  for (int64_t i = 0; i < n; ++i) dy[i] = 2.0 * (y[i] - (double)target[i]) / (double)n;
+  memset(grads, 0, sizeof(double) * n_params);
+  or_backward(L, F, log2T, res, dims, n_dims, params, xyz, n, dy, grads);
+  or_adam(params, grads, m, v, n_params, t, lr, b1, b2, eps, l2);
+  free(y); free(dy);
+  return loss;
+}
+
+/* ------------------------------------------------------------- sampling -- */
+
+/* Philox4x32-10 counter-based generator from its published definition
+ * (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64 multiplies
+ * with the round multipliers 0xD2511F53 / 0xCD9E8D57, the key bumped by the
+ * Weyl constants 0x9E3779B9 / 0xBB67AE85 between rounds. */
+void or_philox4x32_10(const uint32_t *ctr_in, const uint32_t *key_in, uint32_t *out) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Sec. 4: a training batch of uniform coordinates in [0,1)^3.  Point i of
+ * step s draws Philox with counter (i lo, i hi, s, 0) and key (seed lo, seed
+ * hi); each of the first three words becomes (u >> 8) * 2^-24. */
+void or_sample_points(uint64_t seed, uint32_t step, int64_t first, int64_t n, float *xyz) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t id = (uint64_t)(first + i);
+    uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), step, 0u}, u[4];
+    or_philox4x32_10(ctr, key, u);
+    for (int a = 0; a < 3; ++a) xyz[3 * i + a] = (float)(u[a] >> 8) * (1.0f / 16777216.0f);
+  }
+}
+
+/* Sec. 4 / Sec. 4.1: the ground-truth value at x, interpolated trilinearly
+ * from the voxel and its neighbours.  Voxels are cell centred: q = x*n - 0.5
+ * (FP32, the cell decision), clamped to [0, n-1]; the lower index is capped at
+ * n-2 so the upper one stays inside, and the blend is FP64. */
+static void or_voxel_axis(float x, int nvox, int *i0, double *w) {
+  if (nvox == 1) { *i0 = 0; *w = 0.0; return; }
+  float q = x * (float)nvox;
+  q = q - 0.5f;
+  if (q < 0.0f) q = 0.0f;
+  if (q > (float)(nvox - 1)) q = (float)(nvox - 1);
+  int i = (int)floorf(q);
+  if (i > nvox - 2) i = nvox - 2;
+  *i0 = i;
+  *w = (double)q - (double)i;
+}
+
+double or_trilinear_point(const float *vol, int nx, int ny, int nz, const float *x) {
+  int i0[3]; double w[3];
+  or_voxel_axis(x[0], nx, &i0[0], &w[0]);
+  or_voxel_axis(x[1], ny, &i0[1], &w[1]);
+  or_voxel_axis(x[2], nz, &i0[2], &w[2]);
+  double s = 0.0;
+  for (int d = 0; d < 8; ++d) {
+    int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+    int ix = i0[0] + (nx > 1 ? dx : 0), iy = i0[1] + (ny > 1 ? dy : 0), iz = i0[2] + (nz > 1 ? dz : 0);
+    double wt = (dx ? w[0] : 1.0 - w[0]) * (dy ? w[1] : 1.0 - w[1]) * (dz ? w[2] : 1.0 - w[2]);
+    s += wt * (double)vol[((int64_t)iz * ny + iy) * nx + ix];
+  }
+  return s;
+}
+
+void or_trilinear(const float *vol, int nx, int ny, int nz, const float *xyz, int64_t n, double *out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) out[i] = or_trilinear_point(vol, nx, ny, nz, xyz + 3 * i);
+}
+
+/* --------------------------------------------------------- macrocells -- */
+
+/* Sec. 5.3: disjoint macrocells of Ng^3 voxels over the volume (the grid may
+ * overhang it).  Each holds the value range of the voxels a trilinear lookup
+ * inside the cell can touch (voxels Ng*c - 1 .. Ng*c + Ng, clamped) and the
+ * largest opacity mu_max the transfer function reaches on that range: the
+ * maximum LUT alpha over entries floor(255*min) .. ceil(255*max) (FP32
+ * products, the index decision). */
+void or_macrocells(const float *vol, int nx, int ny, int nz, int Ng, const float *lut,
+                   float *minmax, float *mumax) {
+  int ncx = (nx + Ng - 1) / Ng, ncy = (ny + Ng - 1) / Ng, ncz = (nz + Ng - 1) / Ng;
+  for (int cz = 0; cz < ncz; ++cz)
+    for (int cy = 0; cy < ncy; ++cy)
+      for (int cx = 0; cx < ncx; ++cx) {
+        int lo[3] = {cx * Ng - 1, cy * Ng - 1, cz * Ng - 1};
+        int hi[3] = {cx * Ng + Ng, cy * Ng + Ng, cz * Ng + Ng};
+        int nn[3] = {nx, ny, nz};
+        for (int a = 0; a < 3; ++a) {
+          if (lo[a] < 0) lo[a] = 0;
+          if (hi[a] > nn[a] - 1) hi[a] = nn[a] - 1;
+        }
+        float vmin = INFINITY, vmax = -INFINITY;
+        for (int z = lo[2]; z <= hi[2]; ++z)
+          for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+              float v = vol[((int64_t)z * ny + y) * nx + x];
+              if (v < vmin) vmin = v;
+              if (v > vmax) vmax = v;
+            }
+        int64_t c = ((int64_t)cz * ncy + cy) * ncx + cx;
+        minmax[2 * c] = vmin;
+        minmax[2 * c + 1] = vmax;
+        float a0 = vmin < 0.0f ? 0.0f : (vmin > 1.0f ? 1.0f : vmin);
+        float a1 = vmax < 0.0f ? 0.0f : (vmax > 1.0f ? 1.0f : vmax);
+        int e0 = (int)floorf(a0 * 255.0f), e1 = (int)ceilf(a1 * 255.0f);
+        if (e1 > 255) e1 = 255;
+        float mu = 0.0f;
+        for (int e = e0; e <= e1; ++e) if (lut[4 * e + 3] > mu) mu = lut[4 * e + 3];
+        mumax[c] = mu;
+      }
+}
+
+/* ----------------------------------------------------------- renderer -- */
+
+typedef struct {
+  float eye[3], target[3], up[3];
+  float tan_half_fovy; /* > 0: perspective; 0: orthographic */
+  float ortho_w, ortho_h;
+  int width, height;
+} or_camera;
+
+typedef struct {
+  float step;      /* sample spacing along the ray, in units of the unit box */
+  float alpha_exp; /* opacity-correction exponent: step / s1 */
+  float et;        /* early-termination opacity */
+  int mc_cell;     /* macrocell size in voxels (0: no empty-space skipping) */
+} or_opts;
+
+/* A-11: the ray through the centre of pixel (px, py), FP32 operation by
+ * operation (it decides the sample positions).  forward = normalize(target -
+ * eye); right = normalize(up x forward); up' = forward x right; pixel
+ * coordinates u = 2(px+0.5)/W - 1, v = 1 - 2(py+0.5)/H. */
+static void or_norm3(float *a) {
+  float s = a[0] * a[0];
+  s = s + a[1] * a[1];
+  s = s + a[2] * a[2];
+  float len = sqrtf(s);
+  a[0] = a[0] / len; a[1] = a[1] / len; a[2] = a[2] / len;
+}
+
+static void or_cross(const float *a, const float *b, float *c) {
+  float t0 = a[1] * b[2], t1 = a[2] * b[1];
+  c[0] = t0 - t1;
+  t0 = a[2] * b[0]; t1 = a[0] * b[2];
+  c[1] = t0 - t1;
+  t0 = a[0] * b[1]; t1 = a[1] * b[0];
+  c[2] = t0 - t1;
+}
+
+static void or_ray(const or_camera *cam, int px, int py, float *o, float *d) {
+  float fw[3] = {cam->target[0] - cam->eye[0], cam->target[1] - cam->eye[1], cam->target[2] - cam->eye[2]};
+  or_norm3(fw);
+  float rt[3], up2[3];
+  or_cross(cam->up, fw, rt);
+  or_norm3(rt);
+  or_cross(fw, rt, up2);
+  float u = (2.0f * ((float)px + 0.5f)) / (float)cam->width - 1.0f;
+  float v = 1.0f - (2.0f * ((float)py + 0.5f)) / (float)cam->height;
+  if (cam->tan_half_fovy > 0.0f) {
+    float aspect = (float)cam->width / (float)cam->height;
+    float su = u * cam->tan_half_fovy;
+    su = su * aspect;
+    float sv = v * cam->tan_half_fovy;
+    for (int a = 0; a < 3; ++a) {
+      float t0 = su * rt[a];
+      float t1 = sv * up2[a];
+      float s = fw[a] + t0;
+      d[a] = s + t1;
+      o[a] = cam->eye[a];
+    }
+    or_norm3(d);
+  } else {
+    float hu = u * cam->ortho_w;
+    hu = hu * 0.5f;
+    float hv = v * cam->ortho_h;
+    hv = hv * 0.5f;
+    for (int a = 0; a < 3; ++a) {
+      float t0 = hu * rt[a];
+      float t1 = hv * up2[a];
+      float s = cam->eye[a] + t0;
+      o[a] = s + t1;
+      d[a] = fw[a];
+    }
+  }
+}
+
+/* A-11: slab test against [0,1]^3, clipped to t >= 0 (FP32; NaN from 0*inf is
+ * ignored by fminf/fmaxf). */
+static int or_box(const float *o, const float *d, float *t0, float *t1) {
+  float tn = 0.0f, tf = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    float inv = 1.0f / d[a];
+    float ta = (0.0f - o[a]) * inv;
+    float tb = (1.0f - o[a]) * inv;
+    tn = fmaxf(tn, fminf(ta, tb));
+    tf = fminf(tf, fmaxf(ta, tb));
+  }
+  *t0 = tn; *t1 = tf;
+  return tn < tf;
+}
+
+/* A-14: transfer-function lookup, linear between the 256 LUT entries. */
+static void or_tf(const float *lut, double v, double *rgba) {
+  double u = (v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v)) * 255.0;
+  int i = (int)floor(u);
+  if (i > 254) i = 254;
+  double w = u - (double)i;
+  for (int c = 0; c < 4; ++c) rgba[c] = (1.0 - w) * (double)lut[4 * i + c] + w * (double)lut[4 * (i + 1) + c];
+}
+
+/* Sec. 5 / 5.2.1 / 5.3: emission-absorption ray march of selected pixels, one
+ * ray at a time, every sample evaluated in order (the straightforward march
+ * the streaming renderer is compared against, as the paper checks its
+ * streaming path against a megakernel).  Samples sit at t_k = t0 +
+ * (k + 1/2) step while t_k < t1; a sample whose macrocell has mu_max == 0 is
+ * skipped; the value comes from the network (use_net) or from the raw volume
+ * by trilinear interpolation; alpha is corrected as 1 - (1 - alpha)^(step/s1);
+ * front-to-back: C += (1-A) alpha rgb, A += (1-A) alpha; the ray stops once
+ * A >= et. */
+void or_render_pixels(const or_camera *cam, const float *lut, const or_opts *opt,
+                      int use_net, int L, int F, int log2T, const int *res, const int *dims, int n_dims,
+                      const double *params,
+                      const float *vol, int nx, int ny, int nz, const float *mumax,
+                      const int64_t *pix, int64_t npix, double *rgba_out) {
+  int64_t T = (int64_t)1 << log2T;
+  const double *weights = use_net ? params + (int64_t)L * T * F : NULL;
+  int alen = use_net ? or_act_len(dims, n_dims) : 1;
+  int Ng = opt->mc_cell;
+  int ncx = 1, ncy = 1, ncz = 1;
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  if (Ng > 0) {
+    ncx = (nx + Ng - 1) / Ng; ncy = (ny + Ng - 1) / Ng; ncz = (nz + Ng - 1) / Ng;
+    sx = (float)nx / (float)Ng; sy = (float)ny / (float)Ng; sz = (float)nz / (float)Ng;
+  }
+#pragma omp parallel
+  {
+    double *act = (double *)malloc(sizeof(double) * alen);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t q = 0; q < npix; ++q) {
+      int64_t p = pix[q];
+      int px = (int)(p % cam->width), py = (int)(p / cam->width);
+      float o[3], d[3], t0, t1;
+      double C[3] = {0, 0, 0}, A = 0.0;
+      or_ray(cam, px, py, o, d);
+      if (or_box(o, d, &t0, &t1)) {
+        for (int64_t k = 0;; ++k) {
+          float tk = ((float)k + 0.5f) * opt->step;
+          tk = t0 + tk;
+          if (!(tk < t1)) break;
+          float pos[3];
+          for (int a = 0; a < 3; ++a) { float s = tk * d[a]; pos[a] = o[a] + s; }
+          if (Ng > 0) {
+            int cx = (int)floorf(pos[0] * sx), cy = (int)floorf(pos[1] * sy), cz = (int)floorf(pos[2] * sz);
+            cx = cx < 0 ? 0 : (cx > ncx - 1 ? ncx - 1 : cx);
+            cy = cy < 0 ? 0 : (cy > ncy - 1 ? ncy - 1 : cy);
+            cz = cz < 0 ? 0 : (cz > ncz - 1 ? ncz - 1 : cz);
+            if (mumax[((int64_t)cz * ncy + cy) * ncx + cx] == 0.0f) continue;
+          }
+          double val;
+          if (use_net) {
+            or_encode_point(L, F, log2T, res, params, pos, act);
+            val = or_mlp_point(dims, n_dims, weights, act);
+          } else {
+            val = or_trilinear_point(vol, nx, ny, nz, pos);
+          }
+          double c[4];
+          or_tf(lut, val, c);
+          double a = 1.0 - pow(1.0 - c[3], (double)opt->alpha_exp);
+          for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * a * c[ch];
+          A += (1.0 - A) * a;
+          if (A >= (double)opt->et) break;
+        }
+      }
+      rgba_out[4 * q + 0] = C[0];
+      rgba_out[4 * q + 1] = C[1];
+      rgba_out[4 * q + 2] = C[2];
+      rgba_out[4 * q + 3] = A;
+    }
+    free(act);
+  }
+}
+
+/* Ray geometry of one pixel, exposed so tests can pin the camera model. */
+int or_pixel_ray(const or_camera *cam, int px, int py, float *o, float *d, float *t01) {
+  or_ray(cam, px, py, o, d);
+  return or_box(o, d, &t01[0], &t01[1]);
+}
+
+/* ------------------------------------------------------------- quality -- */
+
+/* A-16: mean squared error in FP64 and PSNR with peak 1 (Sec. 7: PSNR of the
+ * decoded volume and of rendered images). */
+double or_mse(const double *a, const double *b, int64_t n) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) { double d = a[i] - b[i]; s += d * d; }
+  return n > 0 ? s / (double)n : 0.0;
+}
+
+double or_psnr(double mse) { return 10.0 * log10(1.0 / mse); }
+
+/* Sec. 5 / Sec. 7: decode the network at every voxel centre (i + 1/2)/n
+ * (FP32 division, the position), and the MSE against the raw volume. */
+double or_volume_mse(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
+                     const double *params, const float *vol, int nx, int ny, int nz) {
+  int64_t T = (int64_t)1 << log2T;
+  const double *weights = params + (int64_t)L * T * F;
+  int alen = or_act_len(dims, n_dims);
+  int64_t nvox = (int64_t)nx * ny * nz;
+  double total = 0.0;
+#pragma omp parallel reduction(+ : total)
+  {
+    double *act = (double *)malloc(sizeof(double) * alen);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < nvox; ++i) {
+      int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((int64_t)nx * ny));
+      float x[3] = {((float)ix + 0.5f) / (float)nx, ((float)iy + 0.5f) / (float)ny, ((float)iz + 0.5f) / (float)nz};
+      or_encode_point(L, F, log2T, res, params, x, act);
+      double yv = or_mlp_point(dims, n_dims, weights, act);
+      double dlt = yv - (double)vol[i];
+      total += dlt * dlt;
+    }
+    free(act);
+  }
+  return nvox > 0 ? total / (double)nvox : 0.0;
+}

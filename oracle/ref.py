@@ -1,0 +1,340 @@
+"""ctypes marshalling for the FP64 oracle in ``oracle.c`` (test infrastructure).
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+legs use this module.  It holds no arithmetic of the method: every function
+converts numpy arrays and calls the C routine of the same name.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cam(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3),
+                ("tan_half_fovy", C.c_float), ("ortho_w", C.c_float), ("ortho_h", C.c_float),
+                ("width", C.c_int), ("height", C.c_int)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("step", C.c_float), ("alpha_exp", C.c_float), ("et", C.c_float),
+                ("mc_cell", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build_oracle())
+        L = _lib
+        L.or_num_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
+        L.or_level_res.argtypes = [C.c_int, C.c_int, C.c_double, _i32p]
+        L.or_hash.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_uint32]
+        L.or_hash.restype = C.c_uint32
+        L.or_param_count_dense_coarse.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                                  C.c_int, C.c_int, C.c_int]
+        L.or_param_count_dense_coarse.restype = C.c_int64
+        L.or_hash_indices.argtypes = [C.c_int, C.c_int, _i32p, _f32p, C.c_int64, _u32p]
+        L.or_encode.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _f64p, _f32p, C.c_int64, _f64p]
+        L.or_mlp_forward.argtypes = [_i32p, C.c_int, _f64p, _f64p, C.c_int64, _f64p]
+        L.or_forward.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
+                                 C.c_int64, _f64p]
+        L.or_loss_l2.argtypes = [_f64p, _f32p, C.c_int64]
+        L.or_loss_l2.restype = C.c_double
+        L.or_backward.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
+                                  C.c_int64, _f64p, _f64p]
+        L.or_adam.argtypes = [_f64p, _f64p, _f64p, _f64p, C.c_int64, C.c_int, C.c_double,
+                              C.c_double, C.c_double, C.c_double, C.c_double]
+        L.or_train_step.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f64p,
+                                    _f64p, _f64p, C.c_int64, _f32p, _f32p, C.c_int64, C.c_int,
+                                    C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.or_train_step.restype = C.c_double
+        L.or_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.or_sample_points.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int64, _f32p]
+        L.or_trilinear.argtypes = [_f32p, C.c_int, C.c_int, C.c_int, _f32p, C.c_int64, _f64p]
+        L.or_macrocells.argtypes = [_f32p, C.c_int, C.c_int, C.c_int, C.c_int, _f32p, _f32p, _f32p]
+        L.or_render_pixels.argtypes = [C.POINTER(_Cam), _f32p, C.POINTER(_Opts), C.c_int, C.c_int,
+                                       C.c_int, C.c_int, _i32p, _i32p, C.c_int, C.c_void_p,
+                                       C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, _i64p,
+                                       C.c_int64, _f64p]
+        L.or_pixel_ray.argtypes = [C.POINTER(_Cam), C.c_int, C.c_int, _f32p, _f32p, _f32p]
+        L.or_pixel_ray.restype = C.c_int
+        L.or_mse.argtypes = [_f64p, _f64p, C.c_int64]
+        L.or_mse.restype = C.c_double
+        L.or_psnr.argtypes = [C.c_double]
+        L.or_psnr.restype = C.c_double
+        L.or_volume_mse.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
+                                    C.c_int, C.c_int, C.c_int]
+        L.or_volume_mse.restype = C.c_double
+    return _lib
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+@dataclass
+class Net:
+    """Shape of a hash-encoded network: L levels, F features, T = 2^log2T."""
+    L: int
+    F: int
+    log2T: int
+    Nmin: int
+    b: float
+    dims: tuple
+
+    @property
+    def T(self) -> int:
+        return 1 << self.log2T
+
+    @property
+    def res(self) -> np.ndarray:
+        return level_res(self.L, self.Nmin, self.b)
+
+    @property
+    def n_table(self) -> int:
+        return self.L * self.T * self.F
+
+    @property
+    def n_weights(self) -> int:
+        d = self.dims
+        return sum(d[k] * d[k + 1] for k in range(len(d) - 1))
+
+    @property
+    def n_params(self) -> int:
+        return self.n_table + self.n_weights
+
+    def _dims(self):
+        return np.asarray(self.dims, dtype=np.int32)
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def level_res(L, Nmin, b):
+    out = np.zeros(L, dtype=np.int32)
+    lib().or_level_res(L, Nmin, float(b), out)
+    return out
+
+
+def hash_vertex(vx, vy, vz, T):
+    return int(lib().or_hash(int(vx), int(vy), int(vz), int(T)))
+
+
+def param_count_dense_coarse(L, F, log2T, base, scale, n_neurons, n_hidden, out_pad=16):
+    return int(lib().or_param_count_dense_coarse(L, F, log2T, base, float(scale), n_neurons,
+                                                 n_hidden, out_pad))
+
+
+def hash_indices(net: Net, xyz):
+    xyz = _f32(xyz)
+    n = xyz.shape[0]
+    out = np.zeros((n, net.L, 8), dtype=np.uint32)
+    lib().or_hash_indices(net.L, net.log2T, net.res, xyz, n, out)
+    return out
+
+
+def encode(net: Net, params, xyz):
+    xyz = _f32(xyz)
+    n = xyz.shape[0]
+    out = np.zeros((n, net.L * net.F), dtype=np.float64)
+    lib().or_encode(net.L, net.F, net.log2T, net.res, _f64(params), xyz, n, out)
+    return out
+
+
+def mlp_forward(dims, weights, inputs):
+    inputs = _f64(inputs)
+    n = inputs.shape[0]
+    out = np.zeros(n, dtype=np.float64)
+    lib().or_mlp_forward(np.asarray(dims, dtype=np.int32), len(dims), _f64(weights), inputs, n, out)
+    return out
+
+
+def forward(net: Net, params, xyz):
+    xyz = _f32(xyz)
+    n = xyz.shape[0]
+    out = np.zeros(n, dtype=np.float64)
+    lib().or_forward(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims), _f64(params),
+                     xyz, n, out)
+    return out
+
+
+def loss_l2(y, t):
+    return float(lib().or_loss_l2(_f64(y), _f32(t), len(y)))
+
+
+def backward(net: Net, params, xyz, dL_dy):
+    xyz = _f32(xyz)
+    g = np.zeros(net.n_params, dtype=np.float64)
+    lib().or_backward(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims), _f64(params),
+                      xyz, xyz.shape[0], _f64(dL_dy), g)
+    return g
+
+
+def adam(p, g, m, v, t, lr=1e-2, b1=0.9, b2=0.999, eps=1e-15, l2=0.0):
+    """In place on p, m, v (float64 arrays)."""
+    lib().or_adam(p, _f64(g), m, v, p.shape[0], int(t), lr, b1, b2, eps, l2)
+
+
+class Trainer:
+    """Oracle training state: FP64 params, Adam moments and the step count."""
+
+    def __init__(self, net: Net, params, lr=1e-2, b1=0.9, b2=0.999, eps=1e-15, l2=0.0):
+        self.net = net
+        self.params = _f64(params).copy()
+        self.grads = np.zeros_like(self.params)
+        self.m = np.zeros_like(self.params)
+        self.v = np.zeros_like(self.params)
+        self.t = 0
+        self.hp = (lr, b1, b2, eps, l2)
+
+    def step(self, xyz, target):
+        net = self.net
+        self.t += 1
+        xyz = _f32(xyz)
+        return float(lib().or_train_step(net.L, net.F, net.log2T, net.res, net._dims(),
+                                         len(net.dims), self.params, self.grads, self.m, self.v,
+                                         net.n_params, xyz, _f32(target), xyz.shape[0], self.t,
+                                         *self.hp))
+
+
+def philox4x32_10(ctr, key):
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(np.asarray(ctr, dtype=np.uint32), np.asarray(key, dtype=np.uint32), out)
+    return out
+
+
+def sample_points(seed, step, first, n):
+    out = np.zeros((n, 3), dtype=np.float32)
+    lib().or_sample_points(int(seed), int(step), int(first), int(n), out)
+    return out
+
+
+def trilinear(vol, xyz):
+    vol = _f32(vol)
+    nz, ny, nx = vol.shape
+    xyz = _f32(xyz)
+    out = np.zeros(xyz.shape[0], dtype=np.float64)
+    lib().or_trilinear(vol, nx, ny, nz, xyz, xyz.shape[0], out)
+    return out
+
+
+def macrocells(vol, cell, lut):
+    vol = _f32(vol)
+    nz, ny, nx = vol.shape
+    nc = (-(-nz // cell), -(-ny // cell), -(-nx // cell))
+    mm = np.zeros(nc + (2,), dtype=np.float32)
+    mu = np.zeros(nc, dtype=np.float32)
+    lib().or_macrocells(vol, nx, ny, nz, cell, _f32(lut), mm, mu)
+    return mm, mu
+
+
+def _cam(cam: dict) -> _Cam:
+    c = _Cam()
+    for k in ("eye", "target", "up"):
+        getattr(c, k)[:] = [float(v) for v in cam[k]]
+    c.tan_half_fovy = float(cam.get("tan_half_fovy", 0.0))
+    c.ortho_w = float(cam.get("ortho_w", 1.0))
+    c.ortho_h = float(cam.get("ortho_h", 1.0))
+    c.width = int(cam["width"])
+    c.height = int(cam["height"])
+    return c
+
+
+def pixel_ray(cam: dict, px, py):
+    o = np.zeros(3, np.float32)
+    d = np.zeros(3, np.float32)
+    t = np.zeros(2, np.float32)
+    hit = lib().or_pixel_ray(C.byref(_cam(cam)), int(px), int(py), o, d, t)
+    return bool(hit), o, d, t
+
+
+def render_pixels(cam: dict, lut, opts: dict, pixels, net: Net | None = None, params=None,
+                  vol=None, mumax=None):
+    """RGBA (FP64) of the listed pixels; network values if net is given, else the raw volume.
+
+    vol (with its dims) is also needed for macrocell skipping when mc_cell > 0."""
+    o = _Opts()
+    o.step = float(opts["step"])
+    o.alpha_exp = float(opts.get("alpha_exp", 1.0))
+    o.et = float(opts.get("et", 0.99))
+    o.mc_cell = int(opts.get("mc_cell", 0))
+    pix = np.ascontiguousarray(pixels, dtype=np.int64)
+    out = np.zeros((pix.shape[0], 4), dtype=np.float64)
+    if vol is not None:
+        vol = _f32(vol)
+        nz, ny, nx = vol.shape
+        volp = vol.ctypes.data
+    else:
+        nz, ny, nx = opts.get("dims", (1, 1, 1))
+        volp = None
+    mup = None
+    if o.mc_cell > 0:
+        mumax = _f32(mumax)
+        mup = mumax.ctypes.data
+    if net is not None:
+        prm = _f64(params)
+        lib().or_render_pixels(C.byref(_cam(cam)), _f32(lut), C.byref(o), 1, net.L, net.F, net.log2T,
+                               net.res, net._dims(), len(net.dims), prm.ctypes.data, volp, nx, ny,
+                               nz, mup, pix, pix.shape[0], out)
+    else:
+        z = np.zeros(1, np.int32)
+        lib().or_render_pixels(C.byref(_cam(cam)), _f32(lut), C.byref(o), 0, 0, 0, 0, z, z, 0, None,
+                               volp, nx, ny, nz, mup, pix, pix.shape[0], out)
+    return out
+
+
+def mse(a, b):
+    a = _f64(a).ravel()
+    b = _f64(b).ravel()
+    return float(lib().or_mse(a, b, a.shape[0]))
+
+
+def psnr(m):
+    return float(lib().or_psnr(float(m)))
+
+
+def volume_mse(net: Net, params, vol):
+    vol = _f32(vol)
+    nz, ny, nx = vol.shape
+    return float(lib().or_volume_mse(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims),
+                                     _f64(params), vol, nx, ny, nz))

@@ -1,0 +1,416 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks one oracle function against something other than itself:
+values the paper prints, hand-derived vectors, closed forms, brute force,
+library routines (numpy / scipy) or finite differences.  No GPU needed.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import ndimage
+
+import oracle as O
+from paper_2207_11620_gb300 import inputs as I
+
+
+def _read_table(path):
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------- encoding ----
+
+def test_level_resolutions_exact():
+    # N_l = floor(Nmin b^l) in exact rational arithmetic (Sec. 3.1, Fig. 1B)
+    for nmin, b, L in [(16, "1.5", 8), (16, "1.38", 16), (4, "2", 10)]:
+        want = [math.floor(Fraction(nmin) * Fraction(b) ** l) for l in range(L)]
+        assert list(O.level_res(L, nmin, float(b))) == want
+
+
+def test_param_counts_match_paper(golden_dir):
+    rows = _read_table(os.path.join(golden_dir, "paper_param_counts.txt"))
+    assert len(rows) == 7
+    for name, L, F, t, base, W, h, count in rows:
+        got = O.param_count_dense_coarse(int(L), int(F), int(t), int(base), 2.0, int(W), int(h), 16)
+        assert got == int(count), name
+
+
+def test_hash_vertices_golden(golden_dir):
+    rows = _read_table(os.path.join(golden_dir, "hash_vertices.txt"))
+    for vx, vy, vz, h in rows:
+        full = int(h, 16)
+        assert O.hash_vertex(int(vx), int(vy), int(vz), 1 << 32 - 1) == full % (1 << 31)
+        for log2T in (4, 14, 19, 22):
+            assert O.hash_vertex(int(vx), int(vy), int(vz), 1 << log2T) == full % (1 << log2T)
+
+
+def test_hash_indices_corner_order():
+    # corner d = dx + 2 dy + 4 dz of the cell floor(fl32(x N_l)) at every level
+    net = O.Net(L=3, F=2, log2T=10, Nmin=4, b=2.0, dims=(6, 8, 1))
+    x = np.array([[0.30, 0.55, 0.81]], np.float32)
+    idx = O.hash_indices(net, x)
+    for l, N in enumerate(net.res):
+        c = [math.floor(float(np.float32(x[0, a]) * np.float32(N))) for a in range(3)]
+        for d in range(8):
+            v = (c[0] + (d & 1), c[1] + ((d >> 1) & 1), c[2] + ((d >> 2) & 1))
+            assert idx[0, l, d] == O.hash_vertex(*v, net.T)
+
+
+def test_encode_at_vertices_returns_table_entries():
+    # at a grid vertex the trilinear weights collapse onto one corner
+    net = O.Net(L=4, F=2, log2T=12, Nmin=16, b=2.0, dims=(8, 16, 1))
+    params = I.uniform_params(net.n_params, seed=11)
+    tab = params[: net.n_table].astype(np.float64).reshape(net.L, net.T, net.F)
+    rng = np.random.default_rng(0)
+    ijk = rng.integers(0, 16, size=(64, 3))
+    x = (ijk / 16.0).astype(np.float32)
+    f = O.encode(net, params, x)
+    for p in range(len(x)):
+        for l, N in enumerate(net.res):
+            c = ijk[p] * (N // 16)
+            h = O.hash_vertex(*c, net.T)
+            assert np.array_equal(f[p, l * 2:(l + 1) * 2], tab[l, h])
+
+
+def test_encode_reproduces_affine_field():
+    # trilinear interpolation is exact for affine fields (tiny grid, no collisions)
+    net = O.Net(L=1, F=2, log2T=12, Nmin=4, b=2.0, dims=(2, 4, 1))
+    N = 4
+    tab = np.zeros((net.T, 2))
+    used = set()
+    a1, a2 = np.array([0.3, -1.2, 0.7]), np.array([2.0, 0.5, -0.25])
+    for vx in range(N + 1):
+        for vy in range(N + 1):
+            for vz in range(N + 1):
+                h = O.hash_vertex(vx, vy, vz, net.T)
+                assert h not in used
+                used.add(h)
+                v = np.array([vx, vy, vz], float)
+                tab[h] = [a1 @ v + 0.1, a2 @ v - 0.4]
+    params = np.concatenate([tab.ravel(), np.zeros(net.n_weights)])
+    x = I.uniform_points(500, seed=5)
+    f = O.encode(net, params, x)
+    p = x.astype(np.float32) * np.float32(N)
+    np.testing.assert_allclose(f[:, 0], p.astype(np.float64) @ a1 + 0.1, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(f[:, 1], p.astype(np.float64) @ a2 - 0.4, rtol=0, atol=1e-12)
+
+
+def test_encode_partition_of_unity():
+    net = O.Net(L=5, F=2, log2T=10, Nmin=16, b=1.5, dims=(10, 8, 1))
+    params = np.concatenate([np.ones(net.n_table), np.zeros(net.n_weights)])
+    f = O.encode(net, params, I.uniform_points(300, seed=2))
+    np.testing.assert_allclose(f, 1.0, rtol=0, atol=1e-14)
+
+
+def test_encode_matches_scipy_trilinear():
+    # brute force: a random field on a collision-free vertex grid, interpolated
+    # by scipy's order-1 map_coordinates at p = x * N
+    net = O.Net(L=1, F=1, log2T=16, Nmin=8, b=2.0, dims=(1, 4, 1))
+    N = 8
+    rng = np.random.default_rng(3)
+    field = rng.normal(size=(N + 1, N + 1, N + 1))  # [vx][vy][vz]
+    tab = np.zeros(net.T)
+    seen = set()
+    for vx in range(N + 1):
+        for vy in range(N + 1):
+            for vz in range(N + 1):
+                h = O.hash_vertex(vx, vy, vz, net.T)
+                assert h not in seen
+                seen.add(h)
+                tab[h] = field[vx, vy, vz]
+    params = np.concatenate([tab, np.zeros(net.n_weights)])
+    x = I.uniform_points(400, seed=9)
+    f = O.encode(net, params, x)[:, 0]
+    p = (x.astype(np.float32) * np.float32(N)).astype(np.float64)
+    want = ndimage.map_coordinates(field, p.T, order=1, mode="nearest")
+    np.testing.assert_allclose(f, want, rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------------------ MLP ----
+
+def test_mlp_matches_numpy_chain():
+    dims = (32, 64, 64, 1)
+    rng = np.random.default_rng(1)
+    Ws = [rng.uniform(-0.3, 0.3, size=(dims[k + 1], dims[k])) for k in range(3)]
+    x = rng.normal(size=(200, 32))
+    h = np.maximum(x @ Ws[0].T, 0)
+    h = np.maximum(h @ Ws[1].T, 0)
+    want = 1.0 / (1.0 + np.exp(-(h @ Ws[2].T)[:, 0]))
+    got = O.mlp_forward(dims, np.concatenate([w.ravel() for w in Ws]), x)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=0)
+
+
+def test_mlp_zero_weights_gives_half():
+    net = O.Net(L=8, F=2, log2T=14, Nmin=16, b=1.5, dims=(16, 64, 64, 1))
+    params = I.uniform_params(net.n_params, seed=1)
+    params[net.n_table:] = 0
+    y = O.forward(net, params, I.uniform_points(100, seed=2))
+    np.testing.assert_array_equal(y, 0.5)
+
+
+# -------------------------------------------------------------- backward ----
+
+def _fd_setup():
+    net = O.Net(L=3, F=2, log2T=8, Nmin=4, b=1.6, dims=(6, 16, 16, 1))
+    params = I.uniform_params(net.n_params, seed=21, scale=0.5).astype(np.float64)
+    x = I.uniform_points(24, seed=22)
+    dy = np.random.default_rng(23).normal(size=24)
+    return net, params, x, dy
+
+
+def test_backward_matches_finite_differences():
+    net, params, x, dy = _fd_setup()
+    g = O.backward(net, params, x, dy)
+
+    def objective(p):
+        return float(dy @ O.forward(net, p, x))
+
+    rng = np.random.default_rng(5)
+    touched = np.flatnonzero(g[: net.n_table])
+    pick = np.concatenate([rng.choice(touched, 40, replace=False),
+                           net.n_table + rng.choice(net.n_weights, 40, replace=False)])
+    eps = 1e-6
+    for i in pick:
+        p1, p2 = params.copy(), params.copy()
+        p1[i] += eps
+        p2[i] -= eps
+        fd = (objective(p1) - objective(p2)) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])) + 1e-9, (i, fd, g[i])
+
+
+def test_backward_directional_derivative():
+    net, params, x, dy = _fd_setup()
+    g = O.backward(net, params, x, dy)
+    d = np.random.default_rng(7).normal(size=net.n_params)
+    eps = 1e-6
+    fp = float(dy @ O.forward(net, params + eps * d, x))
+    fm = float(dy @ O.forward(net, params - eps * d, x))
+    assert abs((fp - fm) / (2 * eps) - g @ d) <= 1e-7 * abs(g @ d) + 1e-9
+
+
+def test_backward_untouched_entries_zero():
+    net, params, x, dy = _fd_setup()
+    g = O.backward(net, params, x, dy)
+    idx = O.hash_indices(net, x)
+    touched = np.zeros((net.L, net.T), bool)
+    for l in range(net.L):
+        touched[l, idx[:, l, :].ravel()] = True
+    gt = g[: net.n_table].reshape(net.L, net.T, net.F)
+    assert np.all(gt[~touched] == 0)
+
+
+# ------------------------------------------------------------------ Adam ----
+
+def test_adam_first_step_is_signed_lr():
+    rng = np.random.default_rng(0)
+    p0 = rng.normal(size=1000)
+    g = rng.normal(size=1000)
+    p, m, v = p0.copy(), np.zeros(1000), np.zeros(1000)
+    O.adam(p, g, m, v, t=1, lr=1e-2, eps=1e-15)
+    # m_hat = g, v_hat = g^2 at t = 1  =>  p1 = p0 - lr g / (|g| + eps)
+    np.testing.assert_allclose(p, p0 - 1e-2 * np.sign(g), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(m, 0.1 * g, rtol=1e-15)
+    np.testing.assert_allclose(v, 0.001 * g * g, rtol=1e-14)
+
+
+def test_adam_large_eps_and_l2():
+    p0 = np.array([0.5, -2.0, 1.0])
+    g = np.array([0.2, 0.0, -3.0])
+    p, m, v = p0.copy(), np.zeros(3), np.zeros(3)
+    O.adam(p, g, m, v, t=1, lr=0.1, eps=1.0, l2=0.0)
+    np.testing.assert_allclose(p, p0 - 0.1 * g / (np.abs(g) + 1.0), rtol=1e-14)
+    p, m, v = p0.copy(), np.zeros(3), np.zeros(3)
+    O.adam(p, np.zeros(3), m, v, t=1, lr=0.1, eps=1e-15, l2=1e-3)
+    np.testing.assert_allclose(p, p0 - 0.1 * np.sign(p0), rtol=1e-12)
+
+
+def test_adam_constant_gradient_stays_signed_lr():
+    # with a constant gradient the bias-corrected moments are exactly g and g^2
+    p0 = np.array([1.0, 1.0])
+    g = np.array([0.25, -4.0])
+    p, m, v = p0.copy(), np.zeros(2), np.zeros(2)
+    for t in range(1, 6):
+        O.adam(p, g, m, v, t=t, lr=1e-2)
+    np.testing.assert_allclose(p, p0 - 5e-2 * np.sign(g), rtol=0, atol=1e-12)
+
+
+def test_train_step_reduces_loss():
+    net = O.Net(L=4, F=2, log2T=10, Nmin=4, b=1.5, dims=(8, 16, 16, 1))
+    params = I.init_params(net.n_table, net.n_weights, seed=3, dims=net.dims)
+    tr = O.Trainer(net, params, lr=1e-2)
+    vol = I.blob_volume(16, seed=3)
+    losses = []
+    for s in range(60):
+        x = O.sample_points(7, s, 0, 512)
+        losses.append(tr.step(x, O.trilinear(vol, x).astype(np.float32)))
+    assert losses[-1] < 0.5 * losses[0]
+
+
+# -------------------------------------------------------------- sampling ----
+
+def test_philox_known_answers(golden_dir):
+    for row in _read_table(os.path.join(golden_dir, "philox4x32_10_kat.txt")):
+        v = [int(t, 16) for t in row]
+        assert list(O.philox4x32_10(v[0:4], v[4:6])) == v[6:10]
+
+
+def test_sample_points_uniform_and_reproducible():
+    a = O.sample_points(1234, 0, 0, 200000)
+    assert a.min() >= 0.0 and a.max() < 1.0
+    assert np.all(np.abs(a.mean(0) - 0.5) < 5e-3)
+    np.testing.assert_array_equal(a[1000:1010], O.sample_points(1234, 0, 1000, 10))
+    assert not np.array_equal(a[:10], O.sample_points(1234, 1, 0, 10))
+    # every coordinate is a multiple of 2^-24 (24 random bits)
+    assert np.all((a * 2 ** 24) == np.floor(a * 2 ** 24))
+
+
+def test_trilinear_at_voxel_centres_and_edges():
+    vol = I.blob_volume((6, 5, 8), seed=2)
+    nz, ny, nx = vol.shape
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    x = np.stack([(ix + 0.5) / nx, (iy + 0.5) / ny, (iz + 0.5) / nz], -1).reshape(-1, 3)
+    got = O.trilinear(vol, x.astype(np.float32))
+    np.testing.assert_array_equal(got, vol.ravel().astype(np.float64))
+    corner = O.trilinear(vol, np.array([[0, 0, 0], [0.9999999, 0.9999999, 0.9999999]], np.float32))
+    assert corner[0] == vol[0, 0, 0] and corner[1] == vol[-1, -1, -1]
+
+
+def test_trilinear_matches_scipy():
+    vol = I.blob_volume(12, seed=4)
+    x = I.uniform_points(1000, seed=8)
+    got = O.trilinear(vol, x)
+    q = (x.astype(np.float32) * np.float32(12) - np.float32(0.5)).astype(np.float64)
+    q = np.clip(q, 0, 11)
+    want = ndimage.map_coordinates(vol.astype(np.float64), q[:, ::-1].T, order=1, mode="nearest")
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------------ macrocells ----
+
+def test_macrocells_brute_force():
+    vol = I.blob_volume((37, 20, 45), seed=6)
+    lut = I.ramp_lut(alpha_floor=0.1)
+    cell = 8
+    mm, mu = O.macrocells(vol, cell, lut)
+    nz, ny, nx = vol.shape
+    for cz in range(mm.shape[0]):
+        for cy in range(mm.shape[1]):
+            for cx in range(mm.shape[2]):
+                sl = tuple(slice(max(0, c * cell - 1), min(n, c * cell + cell + 1))
+                           for c, n in ((cz, nz), (cy, ny), (cx, nx)))
+                blk = vol[sl]
+                assert mm[cz, cy, cx, 0] == blk.min() and mm[cz, cy, cx, 1] == blk.max()
+                lo = int(np.floor(np.float32(blk.min()) * np.float32(255)))
+                hi = min(255, int(np.ceil(np.float32(blk.max()) * np.float32(255))))
+                assert mu[cz, cy, cx] == lut[lo:hi + 1, 3].max()
+
+
+# -------------------------------------------------------------- renderer ----
+
+def test_ortho_rays_through_pixel_centres():
+    cam = I.ortho_camera_z(64, 64)
+    for px, py in [(0, 0), (17, 40), (63, 63)]:
+        hit, o, d, t = O.pixel_ray(cam, px, py)
+        assert hit
+        assert abs(o[0] - (px + 0.5) / 64) < 1e-6 and abs(o[1] - (1 - (py + 0.5) / 64)) < 1e-6
+        assert o[2] == -0.5 and list(d) == [0.0, 0.0, 1.0]
+        assert t[0] == 0.5 and t[1] == 1.5
+
+
+def test_perspective_rays_symmetric():
+    cam = I.perspective_camera(192, 108)
+    _, _, d0, _ = O.pixel_ray(cam, 10, 20)
+    _, _, d1, _ = O.pixel_ray(cam, 181, 20)
+    _, _, d2, _ = O.pixel_ray(cam, 10, 87)
+    assert abs(d0[0] + d1[0]) < 1e-6 and abs(d0[1] - d1[1]) < 1e-6
+    assert abs(d0[1] + d2[1]) < 1e-6
+    assert abs(np.linalg.norm(d0) - 1) < 1e-6
+    # the half-angle of the top edge matches the vertical field of view
+    _, _, dt, _ = O.pixel_ray(cam, 96, 0)
+    ang = math.degrees(math.atan2(dt[1], dt[2]))
+    assert abs(ang - 20.0 * (1 - 1 / 108)) < 0.3
+
+
+def _const_volume(v0, n=8):
+    return np.full((n, n, n), v0, np.float32)
+
+
+@pytest.mark.parametrize("alpha", [0.01, 0.03])
+def test_constant_slab_beer_lambert(alpha):
+    # constant density: A = 1 - (1 - alpha)^(depth / s1) = 1 - exp(-sigma depth),
+    # sigma = -ln(1 - alpha) / s1; colour = rgb * A (emission-absorption)
+    lut = np.zeros((256, 4), np.float32)
+    lut[:, 0], lut[:, 1], lut[:, 2], lut[:, 3] = 0.8, 0.4, 0.2, alpha
+    cam = I.ortho_camera_z(4, 4)
+    steps = 128
+    for s1_steps in (1.0, 2.0):  # s1 = one step, or two steps (alpha_exp = 1/2)
+        opts = dict(step=1.0 / steps, alpha_exp=1.0 / s1_steps, et=0.99)
+        out = O.render_pixels(cam, lut, opts, np.arange(16), vol=_const_volume(0.5))
+        a32 = float(np.float32(alpha))  # the LUT stores alpha in FP32
+        sigma = -math.log(1 - a32) / (s1_steps / steps)
+        A = 1 - math.exp(-sigma * 1.0)
+        np.testing.assert_allclose(out[:, 3], A, rtol=1e-12)
+        np.testing.assert_allclose(out[:, :3], np.broadcast_to(lut[0, :3].astype(np.float64) * A, (16, 3)), rtol=1e-12)
+
+
+def test_early_termination_stops_at_threshold():
+    lut = np.zeros((256, 4), np.float32)
+    lut[:, :] = 0.2
+    cam = I.ortho_camera_z(2, 2)
+    out = O.render_pixels(cam, lut, dict(step=1 / 128, alpha_exp=1.0, et=0.99), np.arange(4),
+                          vol=_const_volume(0.3))
+    keep = 1.0 - float(np.float32(0.2))  # the LUT stores alpha in FP32
+    n_stop = math.ceil(math.log(0.01) / math.log(keep))
+    np.testing.assert_allclose(out[:, 3], 1 - keep ** n_stop, rtol=1e-12)
+
+
+def test_zero_density_is_black():
+    lut = I.ramp_lut()
+    lut[:, 3] = 0
+    cam = I.perspective_camera(8, 6)
+    out = O.render_pixels(cam, lut, dict(step=1 / 64, alpha_exp=0.5), np.arange(48),
+                          vol=I.blob_volume(16, seed=1))
+    assert np.all(out == 0)
+
+
+def test_macrocell_skipping_is_exact_on_raw_volume():
+    # skipped cells have zero opacity over their whole (aproned) value range,
+    # so skipping must not change a raw-volume render at all
+    vol = I.blob_volume(32, seed=4)
+    lut = I.ramp_lut(alpha_floor=0.3)
+    _, mu = O.macrocells(vol, 8, lut)
+    assert (mu == 0).mean() > 0.2
+    cam = I.perspective_camera(48, 32)
+    pix = np.arange(48 * 32)
+    base = dict(step=1 / 64, alpha_exp=0.5, et=0.99)
+    a = O.render_pixels(cam, lut, dict(base, mc_cell=0), pix, vol=vol)
+    b = O.render_pixels(cam, lut, dict(base, mc_cell=8), pix, vol=vol, mumax=mu)
+    np.testing.assert_array_equal(a, b)
+    assert a[:, 3].max() > 0.1
+
+
+# --------------------------------------------------------------- quality ----
+
+def test_psnr_known_values():
+    assert O.psnr(0.01) == pytest.approx(20.0, abs=1e-12)
+    assert O.psnr(1e-3) == pytest.approx(30.0, abs=1e-12)
+    a = np.zeros(1000)
+    b = np.full(1000, 0.1)
+    assert O.mse(a, b) == pytest.approx(0.01, rel=1e-14)
+
+
+def test_volume_mse_zero_weights_closed_form():
+    net = O.Net(L=4, F=2, log2T=10, Nmin=4, b=1.5, dims=(8, 16, 1))
+    params = I.uniform_params(net.n_params, seed=1)
+    params[net.n_table:] = 0
+    vol = I.blob_volume((5, 7, 6), seed=3)
+    want = float(np.mean((0.5 - vol.astype(np.float64)) ** 2))
+    assert O.volume_mse(net, params, vol) == pytest.approx(want, rel=1e-13)
