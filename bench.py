@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Throughput of one hash-encoded neural-volume training step (config 2) on GB300.
+
+A step is one pass of the training hot path over a 2^18-point batch: Philox
+sampling of the points and trilinear ground truth from a 128^3 blob volume,
+hash encoding (L16 F2 T2^19), MLP forward, L2 loss, hand-written backward with
+the table scatter-add, and the dense Adam update of all 16.8 M parameters.
+The metric is training samples per second (decoded samples through the
+forward + backward); the JSON line also carries the dominant kernel's
+roofline, the end-to-end number through the C ABI with host buffers, and the
+FP64 oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp16|bf16] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "decoded samples/s (hash enc+MLP fwd/bwd), 1080p frame ms; PSNR vs FP64 oracle"
+UNIT = "samples/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "fp16", "bf16"])
+    ap.add_argument("--cpu-points", type=int, default=32768, help="oracle sample size (points)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (median SM clock, throttle reasons)."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------- oracle ---
+
+def oracle_step_rate(cpu_points: int):
+    """FP64 oracle on a bounded sample of the config-2 step: one training step on
+    `cpu_points` points plus the dense Adam over all parameters, extrapolated to a
+    2^18-point step.  Returns (samples/s, threads, seconds, description)."""
+    import oracle as O
+    from paper_2207_11620_gb300 import configs as CF
+    from paper_2207_11620_gb300 import inputs as I
+    c = CF.CFG2["net"]
+    net = O.Net(L=c.L, F=c.F, log2T=c.log2T, Nmin=c.Nmin, b=c.b, dims=c.dims)
+    params = I.init_params(net.n_table, net.n_weights, seed=5, dims=c.dims)
+    vol = I.blob_volume(CF.CFG2["volume"], seed=CF.CFG2["volume_seed"])
+    x = O.sample_points(1234, 0, 0, cpu_points)
+    t = O.trilinear(vol, x).astype(np.float32)
+    tr = O.Trainer(net, params)
+    t0 = time.perf_counter()
+    tr.step(x, t)
+    t_step = time.perf_counter() - t0
+    p, g, m, v = tr.params.copy(), tr.grads.copy(), tr.m.copy(), tr.v.copy()
+    t0 = time.perf_counter()
+    O.adam(p, g, m, v, 2)
+    t_adam = time.perf_counter() - t0
+    per_point = max(t_step - t_adam, 1e-12) / cpu_points
+    batch = CF.CFG2["batch"]
+    rate = batch / (t_adam + batch * per_point)
+    desc = (f"one oracle training step on {cpu_points} of the 2^18 config-2 points (forward on "
+            f"{O.num_threads()} threads, backward serial) + one dense Adam over {net.n_params} params; "
+            f"per-point cost extrapolated to a 2^18-point step")
+    return rate, O.num_threads(), t_step + t_adam, desc
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    rates = []
+    secs = 0.0
+    desc = ""
+    threads = 1
+    for i in range(args.warmup + args.steps):
+        r, threads, s, desc = oracle_step_rate(max(1024, args.cpu_points // 4))
+        if i >= args.warmup:
+            rates.append(r)
+            secs += s
+    value = float(statistics.median(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "cfg2 training step: 128^3 blob volume, L16 F2 T2^19 Nmin16 b1.38, "
+                               "MLP 32-64-64-1, 2^18 points, L2, Adam", "global_batch": 1 << 18},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- ours ---
+
+def run_ours(args):
+    import torch
+    from paper_2207_11620_gb300 import build as B
+    from paper_2207_11620_gb300 import configs as CF
+    from paper_2207_11620_gb300 import inputs as I
+    from paper_2207_11620_gb300 import nv
+
+    ws, rank, local = dist_setup(args.gpus)
+    if rank == 0:
+        B.build()
+    barrier(ws)
+    cfg = CF.CFG2
+    c = cfg["net"]
+    prec = args.prec
+    if prec == "auto":
+        prec = "fp16"
+    try:
+        net = nv.NeuralVolume(prec=prec, **c.kwargs())
+    except nv.NvError as e:
+        if args.prec == "auto" and e.status == 6:
+            prec = "fp32"
+            net = nv.NeuralVolume(prec=prec, **c.kwargs())
+        else:
+            raise
+    params = I.init_params(net.n_table, net.n_params - net.n_table, seed=5 + rank, dims=c.dims)
+    net.set_params(params)
+    vol = torch.from_numpy(I.blob_volume(cfg["volume"], seed=cfg["volume_seed"])).cuda()
+    batch = cfg["batch"]
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        net.train_step(n=batch, vol=vol, seed=1000 + rank, loss_out=loss)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    net.profile(True)
+    net.profile_read("mlp"), net.profile_read("adam"), net.profile_read("finish")
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        net.train_step(n=batch, vol=vol, seed=1000 + rank, loss_out=loss)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = ev0.elapsed_time(ev1)
+    net.profile(False)
+    k_mlp = net.profile_read("mlp")
+    k_adam = net.profile_read("adam")
+    k_fin = net.profile_read("finish")
+    ms_max = max_over_ranks(ws, ms)
+    value = ws * batch * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI: batches from pinned host memory, loss read back
+    n_e2e = 4
+    host_x, host_t = [], []
+    for j in range(n_e2e):
+        x, t = nv.sample(vol, batch, seed=77 + rank, step=j)
+        host_x.append(x.cpu().pin_memory())
+        host_t.append(t.cpu().pin_memory())
+    loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    for j in range(2):
+        net.train_step(host_x[j], host_t[j], loss_out=loss)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    e0.record(stream)
+    for i in range(args.steps):
+        net.train_step(host_x[i % n_e2e], host_t[i % n_e2e], loss_out=loss)
+        loss_host.copy_(loss, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier(ws)
+    e2e_ms = max(e0.elapsed_time(e1), 1e3 * t_wall)
+    e2e_ms = max_over_ranks(ws, e2e_ms)
+    e2e_value = ws * batch * args.steps / (e2e_ms / 1e3)
+    clk = clocks.stop()
+    # fresh-run sanity: the loss stays finite
+    assert np.isfinite(loss_host.item())
+
+    if rank != 0:
+        return 0
+    pk, pk_kind = peaks()
+    mlp_avg = k_mlp[0] / max(1, k_mlp[1])
+    adam_avg = k_adam[0] / max(1, k_adam[1])
+    n_params = net.n_params
+    shadow = 2 if prec != "fp32" else 0
+    adam_bytes = n_params * (32 + shadow)
+    if k_adam[0] >= k_mlp[0]:
+        ach = adam_bytes / (adam_avg / 1e3) / 1e9
+        roof = {"kernel": "k_adam", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind,
+                "algorithmic_bytes_per_launch": adam_bytes, "avg_ms": adam_avg}
+    else:
+        # fused sample + encode + MLP forward/backward: count only the MLP MACs
+        d = c.dims
+        fwd = sum(d[k] * d[k + 1] for k in range(len(d) - 1))
+        bwd_x = sum(d[k] * d[k + 1] for k in range(len(d) - 1))
+        flops = 2 * batch * (fwd + bwd_x + fwd)
+        ach = flops / (mlp_avg / 1e3) / 1e12
+        if prec == "fp32":
+            peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"kernel": "k_mlp_f32<TRAIN>", "bound": "alu", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    "algorithmic_flops_per_launch": flops, "avg_ms": mlp_avg}
+        else:
+            peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+            roof = {"kernel": "k_mlp_tc<TRAIN>", "bound": "tensor", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_kind": pk_kind,
+                    "algorithmic_flops_per_launch": flops, "avg_ms": mlp_avg}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[prec], "data": "synthetic",
+        "config": {"workload": "cfg2 training step: 128^3 blob volume, L16 F2 T2^19 Nmin16 b1.38, MLP 32-64-64-1, "
+                               "2^18 points sampled on the GPU, L2 loss, dense Adam",
+                   "global_batch": ws * batch, "mlp_precision": prec, "n_params": n_params,
+                   "l2": "working set > L2: each step's Adam streams params, grads, m, v (269 MB)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roof,
+        "kernels_ms_per_step": {"mlp_fused": mlp_avg, "adam": adam_avg,
+                                "finish": k_fin[0] / max(1, k_fin[1])},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": batch * 16, "d2h_bytes_per_step": 8},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, threads, secs, desc = oracle_step_rate(args.cpu_points)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+                                "seconds": secs}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

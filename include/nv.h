@@ -1,0 +1,224 @@
+/*
+ * nv.h -- C ABI of the GB300 (sm_103a) neural-volume library.
+ *
+ * The library evaluates and trains a multi-resolution hash-encoded neural
+ * volume (Sec. 3.1: L hash tables of T entries x F features, trilinear
+ * interpolation per level, a small ReLU MLP without biases) and renders it
+ * with an emission-absorption ray marcher that streams samples in batches
+ * (Sec. 5.2.1), skips empty macrocells (Sec. 5.3) and stops rays at an
+ * opacity threshold.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an nv_status; NV_OK is 0.  On any other status a
+ *    message is available from nv_last_error() (thread-local, valid until the
+ *    next call on the same thread).  No C++ exception crosses this boundary.
+ *    After NV_ERR_ARG nothing was launched and the context stays usable.
+ *  - Pointers named *_dev are device pointers (cudaMalloc / PyTorch storage)
+ *    owned by the caller.  Pointers named *_any may be host or device memory
+ *    (the library copies with cudaMemcpyDefault).  The library never frees a
+ *    caller pointer.
+ *  - Work is enqueued asynchronously on a CUDA stream: the context's stream
+ *    (nv_create / nv_set_stream) or the `stream` argument (NULL = the legacy
+ *    default stream).  Only nv_sync, nv_get_params and the *_any copies to
+ *    host memory synchronise.
+ *  - Layouts:
+ *      params  one flat float32 vector: tables [L][T][F] (T = 2^log2T),
+ *              then the MLP weights W_0, W_1, ... with W_k stored
+ *              [mlp_dims[k+1]][mlp_dims[k]] row-major (no biases)
+ *      points  [n][3] float32, the normalised domain [0,1)^3 (Sec. 4)
+ *      volume  [nz][ny][nx] float32, x fastest, cell-centred voxels,
+ *              values normalised to [0,1]
+ *      lut     [256][4] float32 RGBA transfer function
+ *      image   [height][width][4] float32 RGBA
+ */
+#ifndef NV_H
+#define NV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nv_ctx nv_ctx;           /* network: params, Adam state, scratch */
+typedef struct nv_renderer nv_renderer; /* ray-streaming buffers of one image size */
+
+typedef enum {
+  NV_OK = 0,
+  NV_ERR_ARG = 1,         /* bad argument; nothing launched */
+  NV_ERR_OOM = 2,         /* device allocation failed */
+  NV_ERR_CUDA = 3,        /* a CUDA call or launch failed */
+  NV_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (kernel returned early) */
+  NV_ERR_STATE = 5,       /* call out of order (e.g. params never set) */
+  NV_ERR_UNSUPPORTED = 6  /* shape or precision this build has no kernel for */
+} nv_status;
+
+typedef enum {
+  NV_FP32 = 0, /* MLP on CUDA cores in FP32 (the parity path) */
+  NV_FP16 = 1, /* MLP on tcgen05 tensor cores, FP16 operands, FP32 accumulate */
+  NV_BF16 = 2  /* MLP on tcgen05 tensor cores, BF16 operands, FP32 accumulate */
+} nv_prec;
+
+typedef enum {
+  NV_BUF_PARAMS = 0, /* FP32 master parameters */
+  NV_BUF_GRADS = 1,  /* FP32 gradient accumulator (zeroed by each optimizer step) */
+  NV_BUF_ADAM_M = 2, /* Adam first moment */
+  NV_BUF_ADAM_V = 3  /* Adam second moment */
+} nv_buffer;
+
+typedef struct {
+  const float *data_dev; /* [nz][ny][nx] */
+  int nx, ny, nz;
+} nv_volume;
+
+typedef struct {
+  float eye[3], target[3], up[3];
+  float tan_half_fovy;   /* tan(vertical fov / 2) > 0: perspective; 0: orthographic */
+  float ortho_w, ortho_h;/* orthographic extent (world units) */
+  int width, height;
+} nv_camera;
+
+typedef struct {
+  float step;      /* sample spacing along a ray, unit-box units (0.5 voxel = 0.5 / n) */
+  float alpha_exp; /* opacity correction exponent step / s1 (Sec. 5.3): a' = 1 - (1 - a)^e */
+  float et;        /* early termination once accumulated opacity >= et (e.g. 0.99) */
+  int K;           /* samples streamed per live ray per iteration (Sec. 5.2.1; ~8) */
+} nv_render_opts;
+
+typedef struct {
+  const float *mu_max_dev; /* [ceil(nz/cell)][ceil(ny/cell)][ceil(nx/cell)] */
+  int cell;                /* macrocell edge in voxels */
+  int nx, ny, nz;          /* volume dimensions the grid was built for */
+} nv_macrocells;
+
+typedef struct {
+  float lr, beta1, beta2, eps, l2_reg;
+} nv_adam_cfg;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a network (Sec. 3.1): L levels, F features per entry, T = 2^log2T
+ * entries per level, level resolution N_l = floor(Nmin * b^l) (FP64 on the
+ * host), MLP widths mlp_dims[0..n_dims-1] with mlp_dims[0] == L*F and
+ * mlp_dims[n_dims-1] == 1 (ReLU hidden layers, sigmoid output, no biases).
+ * prec selects the MLP arithmetic (nv_prec).  Parameters start at zero; Adam
+ * defaults are lr 1e-2, beta (0.9, 0.999), eps 1e-15, l2 0.  Tensor-core
+ * precisions need every hidden width == 64 and mlp_dims[0] in {16, 32, 64}.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  The context
+ * owns every buffer it allocates; nv_destroy frees them. */
+nv_status nv_create(int L, int F, int log2T, int Nmin, double b, const int *mlp_dims, int n_dims,
+                    int prec, void *cuda_stream, nv_ctx **out);
+nv_status nv_destroy(nv_ctx *ctx);
+nv_status nv_set_stream(nv_ctx *ctx, void *cuda_stream);
+/* Sizes: n_params (tables + weights), n_table (L*T*F), and the L level resolutions. */
+nv_status nv_info(const nv_ctx *ctx, int64_t *n_params, int64_t *n_table, int *level_res);
+
+/* Copy all parameters in / out (params_any: [n_params] float32).  Setting also
+ * refreshes the FP16/BF16 shadow copy used by the tensor-core kernels. */
+nv_status nv_set_params(nv_ctx *ctx, const float *params_any);
+nv_status nv_get_params(nv_ctx *ctx, float *params_any);
+/* Device pointer and length of an internal FP32 buffer (nv_buffer); owned by the context. */
+nv_status nv_buffer_ptr(nv_ctx *ctx, int which, float **ptr_dev, int64_t *n);
+/* Adam hyper-parameters (App. B lists beta 0.9 / 0.999, eps 1e-15). */
+nv_status nv_set_adam(nv_ctx *ctx, const nv_adam_cfg *cfg);
+/* Static loss scale S of the FP16/BF16 backward (default 128 / 1).  A step whose
+ * gradient overflows is skipped and S halved, on the device. */
+nv_status nv_set_loss_scale(nv_ctx *ctx, float scale);
+/* Optimizer steps taken (skipped ones not counted) and the current loss scale;
+ * synchronises the context stream. */
+nv_status nv_get_step(nv_ctx *ctx, int *step, float *loss_scale);
+
+/* ---- network evaluation (Sec. 3.1) ---------------------------------------- */
+
+/* A-2 debug output: the 8 corner hash indices of every point at every level,
+ * idx_dev [n][L][8] uint32, corner d = dx + 2dy + 4dz of the cell
+ * floor(fl32(x * N_l)); h = (x*1 ^ y*2654435761 ^ z*805459861) mod T. */
+nv_status nv_hash_indices(nv_ctx *ctx, const float *xyz_dev, int64_t n, uint32_t *idx_dev);
+/* A-1..A-3: the encoded feature vector of each point, feat_dev [n][L*F] float32,
+ * level-major (feature j of level l at l*F + j), from the FP32 master tables. */
+nv_status nv_encode(nv_ctx *ctx, const float *xyz_dev, int64_t n, float *feat_dev);
+/* A-1..A-4: network value y = sigmoid(MLP(encode(x))) of each point, y_dev [n]. */
+nv_status nv_infer(nv_ctx *ctx, const float *xyz_dev, int64_t n, float *y_dev);
+/* A-6/A-7: backward of nv_infer for upstream gradients dL_dy_dev [n]: recomputes
+ * the forward (nothing is stored between the calls) and ADDS the parameter
+ * gradient into dparams_dev [n_params] (NULL: the context's NV_BUF_GRADS). */
+nv_status nv_backward(nv_ctx *ctx, const float *xyz_dev, int64_t n, const float *dL_dy_dev,
+                      float *dparams_dev);
+/* A-8: one Adam step over every parameter (dense) from NV_BUF_GRADS, which it
+ * zeroes; refreshes the FP16/BF16 shadow. */
+nv_status nv_optimizer_step(nv_ctx *ctx);
+
+/* ---- training (Sec. 4) ---------------------------------------------------- */
+
+/* A-9: n training samples, x ~ U[0,1)^3 from Philox4x32-10 (counter (i lo,
+ * i hi, step, 0), key (seed lo, seed hi), coordinate = (u >> 8) 2^-24) and the
+ * target interpolated trilinearly from vol (q = x*n - 0.5, clamped).
+ * xyz_dev [n][3] and target_dev [n] may be NULL to skip either output. */
+nv_status nv_sample(const nv_volume *vol, int64_t n, uint64_t seed, uint32_t step, float *xyz_dev,
+                    float *target_dev, void *stream);
+/* One training step (Sec. 4): forward, L2 loss mean((y - t)^2), backward,
+ * Adam.  Either xyz_any/target_any hold the batch (host or device; host
+ * batches are copied in on the context stream) or both are NULL and the batch
+ * is sampled from vol with nv_sample's generator at the context's sample
+ * counter.  loss_dev (nullable): the batch loss before the update, FP64. */
+nv_status nv_train_step(nv_ctx *ctx, const float *xyz_any, const float *target_any, int64_t n,
+                        const nv_volume *vol, uint64_t seed, double *loss_dev);
+
+/* ---- rendering (Sec. 5) --------------------------------------------------- */
+
+/* A-10: macrocells of `cell` voxels (Sec. 5.3).  minmax_dev [nc][2] holds the
+ * value range of the voxels a trilinear lookup inside the cell can read
+ * (cell*c - 1 .. cell*c + cell, clamped); mu_max_dev [nc] the largest LUT
+ * alpha over entries floor(255 min) .. ceil(255 max).  Either may be NULL. */
+nv_status nv_macrocells_build(const nv_volume *vol, int cell, const float *lut_dev,
+                              float *minmax_dev, float *mu_max_dev, void *stream);
+
+/* A renderer owns the structure-of-arrays ray state for images of up to
+ * max_pixels pixels and K samples per ray per iteration. */
+nv_status nv_renderer_create(int64_t max_pixels, int K, void *cuda_stream, nv_renderer **out);
+nv_status nv_renderer_destroy(nv_renderer *r);
+
+/* A-11..A-15: sample-streaming ray march (Sec. 5.2.1).  Ray generation and
+ * box clipping, then per iteration: the next K sample positions of every live
+ * ray (t_k = t0 + (k + 1/2) step, skipping samples whose macrocell has
+ * mu_max == 0), their values -- from the network `net` (FP32 or tensor-core
+ * inference) or, when net is NULL, from the raw volume `raw` by trilinear
+ * interpolation -- then front-to-back compositing with opacity correction
+ * and early termination, and compaction of the live rays.  mc may be NULL (no
+ * skipping).  rgba_dev [height][width][4]; rays that miss are black. */
+nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
+                    const float *lut_dev, const nv_macrocells *mc, const nv_render_opts *opts,
+                    float *rgba_dev);
+/* Iterations and samples of the last nv_render (synchronises). */
+nv_status nv_render_stats(nv_renderer *r, int *iterations, int64_t *samples);
+
+/* ---- quality (Sec. 7) ------------------------------------------------------ */
+
+/* A-16: FP64 mean squared error over the RGB channels of two images,
+ * mse_dev (one double on the device). */
+nv_status nv_image_mse(const float *rgba_a_dev, const float *rgba_b_dev, int64_t n_pixels,
+                       double *mse_dev, void *stream);
+/* A-16: decode the network at every voxel centre (i + 1/2) / n and the FP64 MSE
+ * against vol, mse_dev (one double on the device).  No decoded grid is stored. */
+nv_status nv_volume_mse(nv_ctx *ctx, const nv_volume *vol, double *mse_dev);
+
+/* ---- misc ------------------------------------------------------------------ */
+
+/* Kernel timing for benchmarks: while enabled, every kernel the context
+ * launches is bracketed by CUDA events on the context stream, grouped by
+ * class (nv_kclass).  nv_profile_read synchronises, returns the summed device
+ * time and launch count of one class since the last read, and clears that
+ * class.  Up to 8192 launches are kept; later ones are not recorded. */
+typedef enum { NV_K_MLP = 0, NV_K_ADAM = 1, NV_K_FINISH = 2, NV_K_RENDER = 3, NV_K_OTHER = 4 } nv_kclass;
+nv_status nv_profile_enable(nv_ctx *ctx, int enable);
+nv_status nv_profile_read(nv_ctx *ctx, int kclass, double *total_ms, int *launches);
+
+/* Wait for the context stream; reports NV_ERR_TIMEOUT if a kernel gave up a wait. */
+nv_status nv_sync(nv_ctx *ctx);
+const char *nv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NV_H */

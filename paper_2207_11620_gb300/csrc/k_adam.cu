@@ -1,0 +1,140 @@
+// k_adam.cu -- A-8: dense Adam over every parameter in one HBM pass.
+//
+// Per parameter the kernel reads p, g, m, v (16 B) and writes p, m, v, g = 0
+// (16 B) plus the FP16/BF16 shadow (2 B) in tensor-core precisions: 32-34 B of
+// algorithmic traffic per parameter, float4-vectorised, grid-stride over a
+// grid of a few CTAs per SM.  The step counter, the overflow flag and the loss
+// scale live on the device, so a step whose gradient overflowed is skipped
+// without a host round trip (the gradient is still cleared).
+#include <algorithm>
+
+#include "nv_internal.cuh"
+
+namespace {
+
+struct AdamHP {
+  float lr, b1, b2, eps, l2;
+};
+
+template <int SHADOW>  // 0 none, 1 fp16, 2 bf16
+__global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__restrict__ g,
+                                              float *__restrict__ m, float *__restrict__ v,
+                                              void *__restrict__ shadow, int64_t n, AdamHP hp,
+                                              const DevState *__restrict__ ds) {
+  const bool skip = ds->overflow != 0;
+  const int t = ds->step + 1;
+  // bias corrections of step t (Kingma & Ba), FP64 then rounded once
+  const float bc1 = (float)(1.0 - pow((double)hp.b1, (double)t));
+  const float bc2 = (float)(1.0 - pow((double)hp.b2, (double)t));
+  const float inv_bc1 = 1.0f / bc1, inv_bc2 = 1.0f / bc2;
+  const int64_t n4 = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float4 *p4 = reinterpret_cast<float4 *>(p), *g4 = reinterpret_cast<float4 *>(g);
+  float4 *m4 = reinterpret_cast<float4 *>(m), *v4 = reinterpret_cast<float4 *>(v);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto upd = [&](float &pp, float gg, float &mm, float &vv) {
+    gg += hp.l2 * pp;
+    mm = hp.b1 * mm + (1.f - hp.b1) * gg;
+    vv = hp.b2 * vv + (1.f - hp.b2) * gg * gg;
+    float mh = mm * inv_bc1, vh = vv * inv_bc2;
+    pp -= hp.lr * mh / (sqrtf(vh) + hp.eps);
+  };
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    float4 gg = __ldcs(g4 + i);
+    __stcs(g4 + i, zero);
+    if (skip) continue;
+    float4 pp = __ldcs(p4 + i), mm = __ldcs(m4 + i), vv = __ldcs(v4 + i);
+    upd(pp.x, gg.x, mm.x, vv.x);
+    upd(pp.y, gg.y, mm.y, vv.y);
+    upd(pp.z, gg.z, mm.z, vv.z);
+    upd(pp.w, gg.w, mm.w, vv.w);
+    p4[i] = pp;
+    __stcs(m4 + i, mm);
+    __stcs(v4 + i, vv);
+    if (SHADOW == 1) {
+      __half2 a = __floats2half2_rn(pp.x, pp.y), b = __floats2half2_rn(pp.z, pp.w);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t *>(&a);
+      u.y = *reinterpret_cast<uint32_t *>(&b);
+      reinterpret_cast<uint2 *>(shadow)[i] = u;
+    } else if (SHADOW == 2) {
+      __nv_bfloat162 a = __floats2bfloat162_rn(pp.x, pp.y), b = __floats2bfloat162_rn(pp.z, pp.w);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t *>(&a);
+      u.y = *reinterpret_cast<uint32_t *>(&b);
+      reinterpret_cast<uint2 *>(shadow)[i] = u;
+    }
+  }
+  // tail (n not a multiple of 4)
+  for (int64_t i = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    float gg = g[i];
+    g[i] = 0.f;
+    if (skip) continue;
+    float pp = p[i], mm = m[i], vv = v[i];
+    upd(pp, gg, mm, vv);
+    p[i] = pp; m[i] = mm; v[i] = vv;
+    if (SHADOW == 1) reinterpret_cast<__half *>(shadow)[i] = __float2half_rn(pp);
+    else if (SHADOW == 2) reinterpret_cast<__nv_bfloat16 *>(shadow)[i] = __float2bfloat16_rn(pp);
+  }
+}
+
+// Book-keeping after the update: count the step or, after an overflow, halve
+// the loss scale; publish the batch loss.
+__global__ void k_step_finish(DevState *ds, double inv_n, double *loss_out) {
+  if (ds->overflow) {
+    ds->loss_scale *= 0.5f;
+    ds->overflow = 0;
+  } else {
+    ds->step += 1;
+  }
+  ds->loss_mean = ds->loss_acc * inv_n;
+  ds->loss_acc = 0.0;
+  if (loss_out) *loss_out = ds->loss_mean;
+}
+
+template <int SHADOW>
+__global__ void k_shadow(const float *__restrict__ p, void *__restrict__ shadow, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (SHADOW == 1) reinterpret_cast<__half *>(shadow)[i] = __float2half_rn(p[i]);
+    else reinterpret_cast<__nv_bfloat16 *>(shadow)[i] = __float2bfloat16_rn(p[i]);
+  }
+}
+
+}  // namespace
+
+nv_status launch_adam(nv_ctx *c) {
+  AdamHP hp{c->adam.lr, c->adam.beta1, c->adam.beta2, c->adam.eps, c->adam.l2_reg};
+  int64_t n = c->n_params;
+  int64_t want = ((n >> 2) + 255) / 256;
+  int64_t grid = (int64_t)c->num_sms * 8;
+  if (want < grid) grid = want;
+  if (grid < 1) grid = 1;
+  switch (c->prec) {
+    case NV_FP16:
+      k_adam<1><<<(unsigned)grid, 256, 0, c->stream>>>(c->params, c->grads, c->adam_m, c->adam_v, c->shadow, n,
+                                                        hp, c->ds);
+      break;
+    case NV_BF16:
+      k_adam<2><<<(unsigned)grid, 256, 0, c->stream>>>(c->params, c->grads, c->adam_m, c->adam_v, c->shadow, n,
+                                                        hp, c->ds);
+      break;
+    default:
+      k_adam<0><<<(unsigned)grid, 256, 0, c->stream>>>(c->params, c->grads, c->adam_m, c->adam_v, nullptr, n, hp,
+                                                        c->ds);
+  }
+  return nv_cuda_check(cudaGetLastError(), "k_adam launch");
+}
+
+nv_status launch_step_finish(nv_ctx *c, double inv_n, double *loss_out) {
+  k_step_finish<<<1, 1, 0, c->stream>>>(c->ds, inv_n, loss_out);
+  return nv_cuda_check(cudaGetLastError(), "k_step_finish launch");
+}
+
+nv_status launch_shadow(nv_ctx *c) {
+  if (c->prec == NV_FP32) return NV_OK;
+  int64_t n = c->n_params;
+  unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
+  if (c->prec == NV_FP16) k_shadow<1><<<grid, 256, 0, c->stream>>>(c->params, c->shadow, n);
+  else k_shadow<2><<<grid, 256, 0, c->stream>>>(c->params, c->shadow, n);
+  return nv_cuda_check(cudaGetLastError(), "k_shadow launch");
+}

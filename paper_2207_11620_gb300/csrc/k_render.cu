@@ -1,0 +1,411 @@
+// k_render.cu -- training-sample generation (A-9), macrocell build (A-10), the
+// sample-streaming ray march (A-11..A-15, Sec. 5.2.1) and the FP64 quality
+// reductions (A-16).
+//
+// Streaming loop per iteration (Sec. 5.2.1, batched ray marching):
+//   k_coords     next K sample positions of each live ray, skipping samples
+//                whose macrocell is transparent (mu_max == 0, Sec. 5.3)
+//   inference    the network on the n_live*K positions (FP32 or tensor-core
+//                kernel), or trilinear lookups of the raw volume
+//   k_composite  front-to-back compositing with opacity correction and early
+//                termination; finished rays write their pixel, live rays are
+//                compacted into the other ray buffer (warp-aggregated atomic)
+// The live count stays on the device: every kernel reads it there, and the
+// host learns it through a pinned copy a few iterations late, so the loop
+// never waits on the GPU inside a frame.
+#include <algorithm>
+#include <cmath>
+
+#include "nv_internal.cuh"
+
+namespace {
+
+enum { R_OX = 0, R_OY, R_OZ, R_DX, R_DY, R_DZ, R_T0, R_T1, R_CR, R_CG, R_CB, R_CA, R_PIX, R_NFIELDS };
+
+__global__ void k_sample(nv_volume v, int64_t n, uint64_t seed, uint32_t step, float *xyz, float *t) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float3 p = nv_sample_point(seed, step, (uint64_t)i);
+  if (xyz) {
+    xyz[3 * i] = p.x;
+    xyz[3 * i + 1] = p.y;
+    xyz[3 * i + 2] = p.z;
+  }
+  if (t) t[i] = nv_trilinear(v.data_dev, v.nx, v.ny, v.nz, p.x, p.y, p.z);
+}
+
+// One CTA per macrocell: min/max over the aproned voxel range, then mu_max
+// from the transfer function over the covered LUT entries.
+__global__ void __launch_bounds__(256) k_macrocells(nv_volume v, int cell, int ncx, int ncy,
+                                                    const float *__restrict__ lut, float *minmax, float *mu) {
+  const int c = blockIdx.x;
+  const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
+  const int x0 = max(cx * cell - 1, 0), x1 = min(cx * cell + cell, v.nx - 1);
+  const int y0 = max(cy * cell - 1, 0), y1 = min(cy * cell + cell, v.ny - 1);
+  const int z0 = max(cz * cell - 1, 0), z1 = min(cz * cell + cell, v.nz - 1);
+  const int wx = x1 - x0 + 1, wy = y1 - y0 + 1, wz = z1 - z0 + 1;
+  const int total = wx * wy * wz;
+  float lo = __int_as_float(0x7f800000), hi = -lo;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    int ix = i % wx, iy = (i / wx) % wy, iz = i / (wx * wy);
+    float val = __ldg(v.data_dev + ((int64_t)(z0 + iz) * v.ny + (y0 + iy)) * v.nx + (x0 + ix));
+    lo = fminf(lo, val);
+    hi = fmaxf(hi, val);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  __shared__ float slo[8], shi[8];
+  if ((threadIdx.x & 31) == 0) {
+    slo[threadIdx.x >> 5] = lo;
+    shi[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      lo = fminf(lo, slo[w]);
+      hi = fmaxf(hi, shi[w]);
+    }
+    if (minmax) {
+      minmax[2 * c] = lo;
+      minmax[2 * c + 1] = hi;
+    }
+    if (mu) {
+      float a0 = fminf(fmaxf(lo, 0.f), 1.f), a1 = fminf(fmaxf(hi, 0.f), 1.f);
+      int e0 = (int)floorf(__fmul_rn(a0, 255.0f)), e1 = min((int)ceilf(__fmul_rn(a1, 255.0f)), 255);
+      float m = 0.f;
+      for (int e = e0; e <= e1; ++e) m = fmaxf(m, lut[4 * e + 3]);
+      mu[c] = m;
+    }
+  }
+}
+
+__device__ __forceinline__ int warp_append(int *counter, bool pred) {
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (mask) {
+    const int leader = __ffs(mask) - 1;
+    if (lane == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+  }
+  return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+__global__ void k_raygen(nv_camera cam, float *ray, int *next_k, int64_t cap, int *count, float4 *rgba) {
+  const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t npix = (int64_t)cam.width * cam.height;
+  bool hit = false;
+  float o[3], d[3], t0 = 0.f, t1 = 0.f;
+  if (pix < npix) {
+    nv_camera_ray(cam, (int)(pix % cam.width), (int)(pix / cam.width), o, d);
+    hit = nv_box(o, d, t0, t1);
+    if (!hit) rgba[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const int slot = warp_append(count, hit);
+  if (hit) {
+    ray[R_OX * cap + slot] = o[0];
+    ray[R_OY * cap + slot] = o[1];
+    ray[R_OZ * cap + slot] = o[2];
+    ray[R_DX * cap + slot] = d[0];
+    ray[R_DY * cap + slot] = d[1];
+    ray[R_DZ * cap + slot] = d[2];
+    ray[R_T0 * cap + slot] = t0;
+    ray[R_T1 * cap + slot] = t1;
+    ray[R_CR * cap + slot] = 0.f;
+    ray[R_CG * cap + slot] = 0.f;
+    ray[R_CB * cap + slot] = 0.f;
+    ray[R_CA * cap + slot] = 0.f;
+    ray[R_PIX * cap + slot] = __int_as_float((int)pix);
+    next_k[slot] = 0;
+  }
+}
+
+struct McView {
+  const float *mu;  // nullptr: no skipping
+  int ncx, ncy, ncz;
+  float sx, sy, sz;  // cells per unit length along each axis (n / cell)
+};
+
+// Next K sample positions of each live ray (A-12).  Sample k sits at
+// t_k = t0 + (k + 1/2) step (FP32, the same operations as the oracle).  A
+// sample inside a transparent macrocell is skipped; the walk jumps to two
+// samples before the cell's exit so every sample near a cell face is still
+// tested on its own, which makes the skipped set exactly the per-sample
+// definition.
+__global__ void k_coords(const float *__restrict__ ray, int *next_k, int64_t cap, const int *count, int K,
+                         float step, McView mc, float *coords, int *nvalid) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *count) return;
+  const float o[3] = {ray[R_OX * cap + i], ray[R_OY * cap + i], ray[R_OZ * cap + i]};
+  const float d[3] = {ray[R_DX * cap + i], ray[R_DY * cap + i], ray[R_DZ * cap + i]};
+  const float t0 = ray[R_T0 * cap + i], t1 = ray[R_T1 * cap + i];
+  int k = next_k[i];
+  int cnt = 0;
+  while (cnt < K) {
+    const float tk = __fadd_rn(t0, __fmul_rn(__fadd_rn((float)k, 0.5f), step));
+    if (!(tk < t1)) break;
+    float pos[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pos[a] = __fadd_rn(o[a], __fmul_rn(tk, d[a]));
+    if (mc.mu) {
+      int cx = min(max((int)floorf(__fmul_rn(pos[0], mc.sx)), 0), mc.ncx - 1);
+      int cy = min(max((int)floorf(__fmul_rn(pos[1], mc.sy)), 0), mc.ncy - 1);
+      int cz = min(max((int)floorf(__fmul_rn(pos[2], mc.sz)), 0), mc.ncz - 1);
+      if (__ldg(mc.mu + ((int64_t)cz * mc.ncy + cy) * mc.ncx + cx) == 0.0f) {
+        // exit distance of this cell along the ray (approximate; only used to jump)
+        const int cc[3] = {cx, cy, cz};
+        const float sc[3] = {mc.sx, mc.sy, mc.sz};
+        float texit = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (d[a] > 0.f) texit = fminf(texit, ((float)(cc[a] + 1) / sc[a] - o[a]) / d[a]);
+          else if (d[a] < 0.f) texit = fminf(texit, ((float)cc[a] / sc[a] - o[a]) / d[a]);
+        }
+        float kf = ceilf((texit - t0) / step - 0.5f) - 2.0f;
+        int kj = k + 1;
+        if (kf > (float)kj) kj = (kf < 2.0e9f) ? (int)kf : 2000000000;
+        k = kj;
+        continue;
+      }
+    }
+    float *dst = coords + (i * K + cnt) * 3;
+    dst[0] = pos[0];
+    dst[1] = pos[1];
+    dst[2] = pos[2];
+    ++cnt;
+    ++k;
+  }
+  for (int j = cnt; j < K; ++j) {
+    float *dst = coords + (i * K + j) * 3;
+    dst[0] = 0.f;
+    dst[1] = 0.f;
+    dst[2] = 0.f;
+  }
+  nvalid[i] = cnt;
+  next_k[i] = k;
+}
+
+__global__ void k_values_raw(nv_volume v, const float *__restrict__ coords, const int *count, int K,
+                             float *values) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)(*count) * K) return;
+  values[i] = nv_trilinear(v.data_dev, v.nx, v.ny, v.nz, coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]);
+}
+
+
+// A-14 + A-15: transfer function (linear between the 256 LUT entries), opacity
+// correction a' = 1 - (1 - a)^e, front-to-back compositing, early termination
+// at A >= et, and compaction of the rays that stay alive.
+__global__ void k_composite(const float *__restrict__ ray, const int *__restrict__ next_k_in, int64_t cap,
+                            const int *count, const float *__restrict__ values, const int *__restrict__ nvalid,
+                            int K, const float *__restrict__ lut, float alpha_exp, float et, float *ray_out,
+                            int *next_k_out, int *count_out, float4 *rgba, unsigned long long *samples) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = *count;
+  bool live = false;
+  int nv = 0;
+  float cr = 0.f, cg = 0.f, cb = 0.f, ca = 0.f;
+  if (i < n) {
+    cr = ray[R_CR * cap + i];
+    cg = ray[R_CG * cap + i];
+    cb = ray[R_CB * cap + i];
+    ca = ray[R_CA * cap + i];
+    nv = nvalid[i];
+    bool done = false;
+    for (int j = 0; j < nv; ++j) {
+      const float v = values[i * K + j];
+      const float u = __fmul_rn(fminf(fmaxf(v, 0.f), 1.f), 255.0f);
+      const int e = min((int)floorf(u), 254);
+      const float w = u - (float)e;
+      const float4 l0 = __ldg(reinterpret_cast<const float4 *>(lut) + e);
+      const float4 l1 = __ldg(reinterpret_cast<const float4 *>(lut) + e + 1);
+      const float r = l0.x + w * (l1.x - l0.x), g = l0.y + w * (l1.y - l0.y), b = l0.z + w * (l1.z - l0.z);
+      const float al = l0.w + w * (l1.w - l0.w);
+      const float ac = (alpha_exp == 1.0f) ? al : 1.0f - powf(1.0f - al, alpha_exp);
+      const float tr = (1.0f - ca) * ac;
+      cr += tr * r;
+      cg += tr * g;
+      cb += tr * b;
+      ca += tr;
+      if (ca >= et) {
+        done = true;
+        break;
+      }
+    }
+    if (nv < K) done = true;  // the ray left the volume during this batch
+    if (done) rgba[__float_as_int(ray[R_PIX * cap + i])] = make_float4(cr, cg, cb, ca);
+    live = !done;
+  }
+  // evaluated samples of this warp, for the statistics
+  int sw = nv;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, o);
+  if ((threadIdx.x & 31) == 0 && sw) atomicAdd(samples, (unsigned long long)sw);
+  const int slot = warp_append(count_out, live);
+  if (live) {
+#pragma unroll
+    for (int f = R_OX; f <= R_T1; ++f) ray_out[f * cap + slot] = ray[f * cap + i];
+    ray_out[R_CR * cap + slot] = cr;
+    ray_out[R_CG * cap + slot] = cg;
+    ray_out[R_CB * cap + slot] = cb;
+    ray_out[R_CA * cap + slot] = ca;
+    ray_out[R_PIX * cap + slot] = ray[R_PIX * cap + i];
+    next_k_out[slot] = next_k_in[i];
+  }
+}
+
+// A-16: FP64 sum of squared RGB differences; each CTA adds its partial / (3n).
+__global__ void __launch_bounds__(256) k_image_mse(const float4 *__restrict__ a, const float4 *__restrict__ b,
+                                                   int64_t n, double scale, double *out) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 x = a[i], y = b[i];
+    double dr = (double)x.x - (double)y.x, dg = (double)x.y - (double)y.y, db = (double)x.z - (double)y.z;
+    s += dr * dr + dg * dg + db * db;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    atomicAdd(out, t * scale);
+  }
+}
+
+__global__ void k_scale_double(double *x, double s) { *x *= s; }
+
+inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
+
+}  // namespace
+
+nv_status launch_scale_double(double *x, double s, cudaStream_t st) {
+  k_scale_double<<<1, 1, 0, st>>>(x, s);
+  return nv_cuda_check(cudaGetLastError(), "k_scale_double launch");
+}
+
+nv_status launch_sample(const nv_volume &v, int64_t n, uint64_t seed, uint32_t step, float *xyz, float *t,
+                        cudaStream_t s) {
+  if (n == 0) return NV_OK;
+  k_sample<<<blocks_for(n, 256), 256, 0, s>>>(v, n, seed, step, xyz, t);
+  return nv_cuda_check(cudaGetLastError(), "k_sample launch");
+}
+
+nv_status launch_macrocells(const nv_volume &v, int cell, const float *lut, float *minmax, float *mu,
+                            cudaStream_t s) {
+  int ncx = (v.nx + cell - 1) / cell, ncy = (v.ny + cell - 1) / cell, ncz = (v.nz + cell - 1) / cell;
+  int64_t nc = (int64_t)ncx * ncy * ncz;
+  k_macrocells<<<(unsigned)nc, 256, 0, s>>>(v, cell, ncx, ncy, lut, minmax, mu);
+  return nv_cuda_check(cudaGetLastError(), "k_macrocells launch");
+}
+
+nv_status launch_image_mse(const float *a, const float *b, int64_t n, double *out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return nv_cuda_check(e, "cudaMemsetAsync");
+  if (n == 0) return NV_OK;
+  unsigned grid = (unsigned)std::min<int64_t>(blocks_for(n, 256), 1216);
+  k_image_mse<<<grid, 256, 0, s>>>(reinterpret_cast<const float4 *>(a), reinterpret_cast<const float4 *>(b), n,
+                                   1.0 / (3.0 * (double)n), out);
+  return nv_cuda_check(cudaGetLastError(), "k_image_mse launch");
+}
+
+nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera &cam, const float *lut,
+                      const nv_macrocells *mc, const nv_render_opts &o, float *rgba) {
+  const int64_t npix = (int64_t)cam.width * cam.height;
+  const int64_t cap = r->max_pixels;
+  const int K = r->K;
+  cudaStream_t st = net ? net->stream : r->stream;
+  cudaError_t e = cudaMemsetAsync(r->counters, 0, 2 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(r->d_samples, 0, sizeof(int64_t), st);
+  if (e != cudaSuccess) return nv_cuda_check(e, "render memset");
+  float4 *out = reinterpret_cast<float4 *>(rgba);
+  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r->ray[0], r->next_k[0], cap, &r->counters[0], out);
+  nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
+  if (s != NV_OK) return s;
+
+  McView mv{nullptr, 1, 1, 1, 0.f, 0.f, 0.f};
+  if (mc) {
+    mv.mu = mc->mu_max_dev;
+    mv.ncx = (mc->nx + mc->cell - 1) / mc->cell;
+    mv.ncy = (mc->ny + mc->cell - 1) / mc->cell;
+    mv.ncz = (mc->nz + mc->cell - 1) / mc->cell;
+    mv.sx = (float)mc->nx / (float)mc->cell;
+    mv.sy = (float)mc->ny / (float)mc->cell;
+    mv.sz = (float)mc->nz / (float)mc->cell;
+  }
+  // every iteration consumes at least one sample of each live ray, or ends it
+  const int64_t max_iter = (int64_t)std::ceil(1.7320509 / (double)o.step / (double)K) + 4;
+  const int R = 4;  // iterations in flight before the host waits for a count
+  cudaEvent_t ev[R];
+  for (int j = 0; j < R; ++j) {
+    e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      for (int q = 0; q < j; ++q) cudaEventDestroy(ev[q]);
+      return nv_cuda_check(e, "cudaEventCreate");
+    }
+  }
+  int64_t bound = npix;  // upper bound of the live rays (counts only decrease)
+  int64_t issued = 0, known = 0;  // iterations launched / whose count the host has read
+  int cur = 0;
+  while (bound > 0 && issued < max_iter) {
+    const int nxt = cur ^ 1;
+    k_coords<<<blocks_for(bound, 128), 128, 0, st>>>(r->ray[cur], r->next_k[cur], cap, &r->counters[cur], K,
+                                                     o.step, mv, r->coords, r->nvalid);
+    if ((s = nv_cuda_check(cudaGetLastError(), "k_coords launch")) != NV_OK) break;
+    if (net) {
+      MlpArgs a{};
+      a.xyz = r->coords;
+      a.y = r->values;
+      a.ds = net->ds;
+      s = (net->prec == NV_FP32)
+              ? launch_mlp_f32_ext(net, MODE_INFER, a, &r->counters[cur], K, bound * K, nullptr)
+              : launch_mlp_tc_ext(net, MODE_INFER, a, &r->counters[cur], K, bound * K, nullptr);
+      if (s != NV_OK) break;
+    } else {
+      k_values_raw<<<blocks_for(bound * K, 256), 256, 0, st>>>(*raw, r->coords, &r->counters[cur], K, r->values);
+      if ((s = nv_cuda_check(cudaGetLastError(), "k_values_raw launch")) != NV_OK) break;
+    }
+    if ((e = cudaMemsetAsync(&r->counters[nxt], 0, sizeof(int), st)) != cudaSuccess) {
+      s = nv_cuda_check(e, "cudaMemsetAsync");
+      break;
+    }
+    k_composite<<<blocks_for(bound, 128), 128, 0, st>>>(
+        r->ray[cur], r->next_k[cur], cap, &r->counters[cur], r->values, r->nvalid, K, lut, o.alpha_exp, o.et,
+        r->ray[nxt], r->next_k[nxt], &r->counters[nxt], out, reinterpret_cast<unsigned long long *>(r->d_samples));
+    if ((s = nv_cuda_check(cudaGetLastError(), "k_composite launch")) != NV_OK) break;
+    const int slot = (int)(issued % R);
+    cudaMemcpyAsync(&r->h_count[slot], &r->counters[nxt], sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(ev[slot], st);
+    ++issued;
+    cur = nxt;
+    // learn counts of finished iterations; block only when R iterations are in flight
+    while (known < issued) {
+      const int ks = (int)(known % R);
+      cudaError_t q = (issued - known >= R) ? cudaEventSynchronize(ev[ks]) : cudaEventQuery(ev[ks]);
+      if (q == cudaErrorNotReady) break;
+      if (q != cudaSuccess) {
+        s = nv_cuda_check(q, "render event");
+        break;
+      }
+      bound = r->h_count[ks];
+      ++known;
+      if (bound == 0) break;
+    }
+    if (s != NV_OK) break;
+  }
+  if (s == NV_OK && bound > 0 && issued >= max_iter) {
+    // the loop stopped on the iteration cap: the last live count decides
+    e = cudaEventSynchronize(ev[(int)((issued - 1) % R)]);
+    if (e != cudaSuccess) s = nv_cuda_check(e, "render event");
+    else if (r->h_count[(int)((issued - 1) % R)] > 0)
+      s = nv_fail(NV_ERR_STATE, "ray march did not finish within %lld iterations", (long long)max_iter);
+  }
+  r->last_iters = (int)issued;
+  for (int j = 0; j < R; ++j) cudaEventDestroy(ev[j]);
+  return s;
+}

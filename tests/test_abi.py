@@ -1,0 +1,79 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+include/nv.h declares, and rejects bad arguments on the host before any launch."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "nv.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:nv_status|const char \*)\s*(nv_\w+)\s*\(", txt, re.M)))
+
+
+@pytest.fixture(scope="module")
+def nvmod():
+    import torch  # noqa: F401  (loads the CUDA runtime libnv.so links against)
+    from paper_2207_11620_gb300 import build, nv
+    build.build()
+    return nv
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("nv_create", "nv_encode", "nv_infer", "nv_backward", "nv_train_step", "nv_render",
+                 "nv_macrocells_build", "nv_sample", "nv_volume_mse", "nv_image_mse", "nv_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(nvmod):
+    lib = nvmod.lib()
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(_declared()) == set(nvmod.EXPORTS)
+
+
+def _create(nvmod, L=8, F=2, log2T=14, Nmin=16, b=1.5, dims=(16, 64, 64, 1), prec=0):
+    arr = (C.c_int * len(dims))(*dims)
+    h = C.c_void_p()
+    st = nvmod.lib().nv_create(L, F, log2T, Nmin, b, arr, len(dims), prec, None, C.byref(h))
+    return st, h, nvmod.lib().nv_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(L=0), "L=0"), (dict(F=3), "F=3"), (dict(log2T=0), "log2T"), (dict(b=0.5), "b=0.5"),
+    (dict(dims=(15, 64, 64, 1)), "mlp_dims[0]"), (dict(dims=(16, 64, 64, 2)), "output width"),
+    (dict(prec=7), "prec=7"), (dict(dims=(16,)), "n_dims"),
+])
+def test_create_rejects_bad_arguments(nvmod, kw, frag):
+    st, h, msg = _create(nvmod, **kw)
+    assert st == 1 and not h.value and frag in msg
+
+
+def test_entry_points_reject_null_context(nvmod):
+    lib = nvmod.lib()
+    assert lib.nv_infer(None, None, 0, None) == 1
+    assert lib.nv_train_step(None, None, None, 1, None, 0, None) == 1
+    assert lib.nv_sync(None) == 1
+    assert lib.nv_destroy(None) == 0
+    assert "ctx is NULL" in lib.nv_last_error().decode()
+
+
+def test_renderer_rejects_bad_arguments(nvmod):
+    lib = nvmod.lib()
+    h = C.c_void_p()
+    assert lib.nv_renderer_create(0, 8, None, C.byref(h)) == 1
+    assert lib.nv_renderer_create(16, 0, None, C.byref(h)) == 1
+    assert lib.nv_render(None, None, None, None, None, None, None, None) == 1
+
+
+def test_sample_rejects_missing_volume(nvmod):
+    lib = nvmod.lib()
+    assert lib.nv_sample(None, 10, 0, 0, None, None, None) == 1
+    v = nvmod.Volume(None, 4, 4, 4)
+    assert lib.nv_sample(C.byref(v), 10, 0, 0, None, None, None) == 1
+    v = nvmod.Volume(1234, 0, 4, 4)
+    assert lib.nv_macrocells_build(C.byref(v), 16, None, None, None, None) == 1
