@@ -21,12 +21,18 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__re
                                               float *__restrict__ m, float *__restrict__ v,
                                               void *__restrict__ shadow, int64_t n, AdamHP hp,
                                               const DevState *__restrict__ ds) {
-  const bool skip = ds->overflow != 0;
-  const int t = ds->step + 1;
-  // bias corrections of step t (Kingma & Ba), FP64 then rounded once
-  const float bc1 = (float)(1.0 - pow((double)hp.b1, (double)t));
-  const float bc2 = (float)(1.0 - pow((double)hp.b2, (double)t));
-  const float inv_bc1 = 1.0f / bc1, inv_bc2 = 1.0f / bc2;
+  // bias corrections of step t (Kingma & Ba): one FP64 evaluation per CTA
+  __shared__ float s_bc[2];
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) {
+    const int t = ds->step + 1;
+    s_bc[0] = (float)(1.0 / (1.0 - pow((double)hp.b1, (double)t)));
+    s_bc[1] = (float)(1.0 / (1.0 - pow((double)hp.b2, (double)t)));
+    s_skip = ds->overflow != 0;
+  }
+  __syncthreads();
+  const bool skip = s_skip != 0;
+  const float inv_bc1 = s_bc[0], inv_bc2 = s_bc[1];
   const int64_t n4 = n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   float4 *p4 = reinterpret_cast<float4 *>(p), *g4 = reinterpret_cast<float4 *>(g);

@@ -224,7 +224,8 @@ __global__ void k_composite(const float *__restrict__ ray, const int *__restrict
       const float4 l1 = __ldg(reinterpret_cast<const float4 *>(lut) + e + 1);
       const float r = l0.x + w * (l1.x - l0.x), g = l0.y + w * (l1.y - l0.y), b = l0.z + w * (l1.z - l0.z);
       const float al = l0.w + w * (l1.w - l0.w);
-      const float ac = (alpha_exp == 1.0f) ? al : 1.0f - powf(1.0f - al, alpha_exp);
+      // a' = 1 - (1 - a)^e, as -expm1(e log1p(-a)) to keep small opacities accurate
+      const float ac = (alpha_exp == 1.0f) ? al : -expm1f(alpha_exp * log1pf(-al));
       const float tr = (1.0f - ca) * ac;
       cr += tr * r;
       cg += tr * g;

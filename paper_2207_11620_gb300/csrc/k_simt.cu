@@ -136,8 +136,9 @@ __host__ __device__ inline SmemPlan plan_smem(const NetDesc &nd, int mode) {
   }
   s.dout_off = off;
   if (mode != MODE_INFER) off += kP;
+  off = (off + 1) & ~1;  // the FP64 accumulator needs 8-byte alignment
   s.gw_off = off;
-  if (mode == MODE_BACKWARD || mode == MODE_TRAIN) off += (int)nd.n_weights;
+  if (mode == MODE_BACKWARD || mode == MODE_TRAIN) off += 2 * (int)nd.n_weights;
   s.total = off;
   return s;
 }
@@ -160,8 +161,10 @@ __global__ void __launch_bounds__(kP) k_mlp_f32(NetDesc nd, const float *__restr
   const int nl = nd.n_dims - 1;
   float *sW = sm;
   for (int64_t i = tid; i < nd.n_weights; i += kP) sW[i] = params[nd.n_table + i];
+  // the CTA's weight-gradient accumulator is FP64: it sums one FP32 partial per tile
+  double *sGW = reinterpret_cast<double *>(sm + sp.gw_off);
   if (MODE == MODE_BACKWARD || MODE == MODE_TRAIN)
-    for (int64_t i = tid; i < nd.n_weights; i += kP) sm[sp.gw_off + i] = 0.f;
+    for (int64_t i = tid; i < nd.n_weights; i += kP) sGW[i] = 0.0;
   __syncthreads();
 
   const int64_t n = n_dev ? (int64_t)(*n_dev) * n_mult : a.n;
@@ -239,7 +242,6 @@ __global__ void __launch_bounds__(kP) k_mlp_f32(NetDesc nd, const float *__restr
     }
     float *sDout = sm + sp.dout_off;
     sDout[tid] = g * yv * (1.f - yv);
-    float *sGW = sm + sp.gw_off;
     // backward, layer by layer from the output
     for (int k = nl - 1; k >= 0; --k) {
       const int din = nd.dims[k], dout = nd.dims[k + 1];
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(kP) k_mlp_f32(NetDesc nd, const float *__restr
         const int j = e / din, i = e - j * din;
         float s = 0.f;
         for (int q = 0; q < kP; ++q) s += dl[q * dstride + j] * act[q * (din + 1) + i];
-        sGW[nd.w_off[k] + e] += s;
+        sGW[nd.w_off[k] + e] += (double)s;
       }
       __syncthreads();
       const float *W = sW + nd.w_off[k];
@@ -289,9 +291,8 @@ __global__ void __launch_bounds__(kP) k_mlp_f32(NetDesc nd, const float *__restr
   }
   if (MODE == MODE_BACKWARD || MODE == MODE_TRAIN) {
     __syncthreads();
-    float *sGW = sm + sp.gw_off;
     for (int64_t i = tid; i < nd.n_weights; i += kP) {
-      float v = sGW[i];
+      float v = (float)sGW[i];
       if (v != 0.f) atomicAdd(a.grads + nd.n_table + i, v);
     }
   }

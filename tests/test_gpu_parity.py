@@ -1,8 +1,10 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
 Tolerances: hash indices and macrocell bounds bit-exact; the FP32 path within
-1e-5 relative error, measured as |g - o| / max(|o|, 1e-3 max|o|) so entries
-that are zero up to rounding do not divide by zero.
+1e-5 relative error, measured per element as |g - o| / max(|o|, 1e-2 max|o|):
+FP32 rounding scales with the magnitude of the summed terms, not with a
+result that cancels to nearly zero, so an element below 1% of the tensor's
+largest is judged against 1% of the largest.
 """
 import math
 
@@ -24,7 +26,7 @@ def rel_err(g, o):
     o = np.asarray(o, np.float64)
     if o.size == 0:
         return 0.0
-    den = np.maximum(np.abs(o), 1e-3 * max(np.abs(o).max(), 1e-30))
+    den = np.maximum(np.abs(o), 1e-2 * max(np.abs(o).max(), 1e-30))
     return float(np.max(np.abs(g - o) / den))
 
 
@@ -83,7 +85,18 @@ def test_infer_cfg1_full_size(nv):
     got = net.infer(torch.from_numpy(x).cuda()).cpu().numpy()
     want = O.forward(onet(cfg["net"]), params, x)
     assert rel_err(got, want) <= FP32_TOL
-    assert np.std(want) > 1e-3  # the outputs are not all the same
+
+
+def test_infer_varied_outputs(nv):
+    cfg = CF.CFG1_NET
+    net = make_net(nv, cfg)
+    params = I.uniform_params(net.n_params, seed=31, scale=1.0)
+    net.set_params(params)
+    x = I.uniform_points(50000, seed=32)
+    got = net.infer(torch.from_numpy(x).cuda()).cpu().numpy()
+    want = O.forward(onet(cfg), params, x)
+    assert np.std(want) > 0.05
+    assert rel_err(got, want) <= FP32_TOL
 
 
 @pytest.mark.parametrize("n", [0, 1, 127, 129, 1000])
@@ -242,15 +255,20 @@ def test_macrocells_bit_exact(nv):
 # --------------------------------------------------------------- rendering ----
 
 def _compare_images(got, want, et=0.99, tol=FP32_TOL):
-    """RGBA per pixel; pixels whose oracle opacity sits at the early-termination
-    threshold may stop one sample apart, which moves them by at most 1 - et."""
+    """RGBA per pixel.  A ray that reaches the early-termination opacity may stop
+    one sample earlier or later on one side when its opacity is within rounding
+    of et; such a pixel moves by at most 1 - et.  Those pixels are allowed that
+    bound (and must be rare); every other pixel meets the FP32 tolerance."""
     got = got.reshape(-1, 4).astype(np.float64)
     want = want.reshape(-1, 4)
-    straddle = np.abs(want[:, 3] - et) < 2e-4
-    ok = ~straddle
-    assert rel_err(got[ok], want[ok]) <= tol
+    den = np.maximum(np.abs(want), 1e-2 * max(np.abs(want).max(), 1e-30))
+    bad = (np.abs(got - want) / den > tol).any(axis=1)
+    term = np.maximum(got[:, 3], want[:, 3]) >= et - 1e-4
+    assert not np.any(bad & ~term), rel_err(got[~term], want[~term])
+    straddle = bad & term
+    assert straddle.sum() <= max(2, 0.01 * len(want))
     assert np.all(np.abs(got[straddle] - want[straddle]) <= (1 - et) + 1e-4)
-    return straddle.sum()
+    return int(straddle.sum())
 
 
 def test_render_cfg1_network_full_image(nv):
