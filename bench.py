@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "fp16", "bf16"])
     ap.add_argument("--cpu-points", type=int, default=32768, help="oracle sample size (points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", default="cfg2_quality,cfg3_render,cfg4_inloop",
+                    help="comma list of extra measurements (empty for none)")
     return ap.parse_args()
 
 
@@ -324,12 +326,164 @@ def run_ours(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
+    if ws == 1 and args.extras:
+        line["extra"] = run_extras(args)
     if ws == 1 and not args.no_cpu_baseline:
         rate, threads, secs, desc = oracle_step_rate(args.cpu_points)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
                                 "seconds": secs}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------- extras ---
+
+def _psnr(mse):
+    import math
+    return 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")
+
+
+def extra_cfg2_quality(nv, I, CF, torch, steps=1000):
+    """Config 2 as specified: 1000 steps of 2^18 points, FP32 vs FP16 MLP; volume PSNR."""
+    cfg = CF.CFG2
+    c = cfg["net"]
+    vol = torch.from_numpy(I.blob_volume(cfg["volume"], seed=cfg["volume_seed"])).cuda()
+    out = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        net = nv.NeuralVolume(prec=prec, **c.kwargs())
+        net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(steps):
+            net.train_step(n=cfg["batch"], vol=vol, seed=31, loss_out=loss)
+        e1.record()
+        torch.cuda.synchronize()
+        mse = net.volume_mse(vol).item()
+        out[prec] = {"steps": steps, "ms_per_step": e0.elapsed_time(e1) / steps, "final_loss": loss.item(),
+                     "volume_psnr_db": _psnr(mse)}
+        net.close()
+    return out
+
+
+def _render_setup(nv, I, torch, cfg, vt):
+    lut = torch.from_numpy(I.ramp_lut(alpha_floor=cfg["alpha_floor"])).cuda()
+    _, mu = nv.macrocells_build(vt, cfg["cell"], lut)
+    D = vt.shape[0]
+    opts = dict(step=cfg["step_voxels"] / D, alpha_exp=cfg["step_voxels"], et=cfg["et"], K=cfg["K"])
+    return lut, mu, opts
+
+
+def _time_render(r, torch, frames, **kw):
+    r.render(**kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(frames):
+        img = r.render(**kw)
+    e1.record()
+    torch.cuda.synchronize()
+    return img, e0.elapsed_time(e1) / frames
+
+
+def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=5):
+    """Config 3: 512^3 volume, T2^21 network trained with config 2's recipe, 1080p
+    perspective march (0.5 voxel, 16^3 macrocells, ET 0.99) with FP16 and BF16
+    inference; PSNR of each neural image against the raw-volume image."""
+    cfg = CF.CFG3
+    c = cfg["net"]
+    D = cfg["volume"]
+    vt = I.blob_volume_torch(D, cfg["volume_seed"], "cuda")
+    lut, mu, opts = _render_setup(nv, I, torch, cfg, vt)
+    W, H = cfg["image"]
+    cam = I.perspective_camera(W, H, cfg["vfov"], cfg["eye"], cfg["target"])
+    mc = (mu, cfg["cell"], vt.shape)
+    r = nv.Renderer(W * H, K=cfg["K"])
+    raw, raw_ms = _time_render(r, torch, frames, cam=cam, lut=lut, opts=opts, raw=vt, mc=mc)
+    raw = raw.clone()
+    it, ns = r.stats()
+    out = {"image": [W, H], "raw_ms": raw_ms, "raw_samples_per_frame": ns, "raw_iterations": it}
+    steps = train_steps or cfg["train_steps"]
+    for prec in ("fp16", "bf16"):
+        net = nv.NeuralVolume(prec=prec, **c.kwargs())
+        net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(steps):
+            net.train_step(n=cfg["batch"], vol=vt, seed=11, loss_out=loss)
+        e1.record()
+        torch.cuda.synchronize()
+        img, ms = _time_render(r, torch, frames, cam=cam, lut=lut, opts=opts, net=net, mc=mc)
+        it, ns = r.stats()
+        mse = nv.image_mse(img, raw).item()
+        out[prec] = {"train_steps": steps, "train_ms_per_step": e0.elapsed_time(e1) / steps,
+                     "frame_ms": ms, "samples_per_frame": ns, "iterations": it,
+                     "decoded_samples_per_s": ns / (ms / 1e3), "image_psnr_db": _psnr(mse),
+                     "volume_psnr_db": _psnr(net.volume_mse(vt).item())}
+        net.close()
+    r.close()
+    del vt
+    torch.cuda.empty_cache()
+    return out
+
+
+def extra_cfg4_inloop(nv, I, CF, torch, frames=None):
+    """Config 4: 1024^3 volume in HBM; each frame one 2^18-point training step and a
+    1024x1024 render of the current FP16 network; ms/frame and the PSNR of the
+    last frame against the raw-volume render."""
+    cfg = CF.CFG4
+    c = cfg["net"]
+    D = cfg["volume"]
+    frames = frames or cfg["frames"]
+    vt = I.blob_volume_torch(D, cfg["volume_seed"], "cuda")
+    lut, mu, opts = _render_setup(nv, I, torch, cfg, vt)
+    W, H = cfg["image"]
+    cam = I.perspective_camera(W, H, 40.0, (0.5, 0.5, -1.0), (0.5, 0.5, 0.5))
+    mc = (mu, cfg["cell"], vt.shape)
+    r = nv.Renderer(W * H, K=cfg["K"])
+    raw, raw_ms = _time_render(r, torch, 2, cam=cam, lut=lut, opts=opts, raw=vt, mc=mc)
+    raw = raw.clone()
+    net = nv.NeuralVolume(prec="fp16", **c.kwargs())
+    net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    psnr_curve = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for f in range(frames):
+        net.train_step(n=cfg["batch"], vol=vt, seed=21, loss_out=loss)
+        r.render(cam, lut, opts, net=net, mc=mc, out=img)
+        if f % 100 == 99:
+            psnr_curve.append((f + 1, nv.image_mse(img, raw)))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / frames
+    curve = [(f, _psnr(m.item())) for f, m in psnr_curve]
+    out = {"frames": frames, "ms_per_frame": ms, "raw_ms": raw_ms, "psnr_db_by_frame": curve,
+           "final_psnr_db": curve[-1][1] if curve else None, "n_params": net.n_params}
+    net.close()
+    r.close()
+    del vt
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_extras(args):
+    import torch
+    from paper_2207_11620_gb300 import configs as CF
+    from paper_2207_11620_gb300 import inputs as I
+    from paper_2207_11620_gb300 import nv
+    out = {}
+    for name, fn in (("cfg2_quality", extra_cfg2_quality), ("cfg3_render", extra_cfg3_render),
+                     ("cfg4_inloop", extra_cfg4_inloop)):
+        if name not in args.extras:
+            continue
+        try:
+            out[name] = fn(nv, I, CF, torch)
+        except Exception as e:  # report and keep the main line
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    return out
 
 
 def main():

@@ -16,6 +16,25 @@ struct AdamHP {
   float lr, b1, b2, eps, l2;
 };
 
+constexpr int kU = 4;  // float4 iterations per thread kept in flight
+
+template <int SHADOW>
+__device__ __forceinline__ void put_shadow(void *shadow, int64_t i, float4 pp) {
+  if (SHADOW == 1) {
+    __half2 a = __floats2half2_rn(pp.x, pp.y), b = __floats2half2_rn(pp.z, pp.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t *>(&a);
+    u.y = *reinterpret_cast<uint32_t *>(&b);
+    reinterpret_cast<uint2 *>(shadow)[i] = u;
+  } else if (SHADOW == 2) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(pp.x, pp.y), b = __floats2bfloat162_rn(pp.z, pp.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t *>(&a);
+    u.y = *reinterpret_cast<uint32_t *>(&b);
+    reinterpret_cast<uint2 *>(shadow)[i] = u;
+  }
+}
+
 template <int SHADOW>  // 0 none, 1 fp16, 2 bf16
 __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__restrict__ g,
                                               float *__restrict__ m, float *__restrict__ v,
@@ -34,51 +53,63 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__re
   const bool skip = s_skip != 0;
   const float inv_bc1 = s_bc[0], inv_bc2 = s_bc[1];
   const int64_t n4 = n >> 2;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  float4 *p4 = reinterpret_cast<float4 *>(p), *g4 = reinterpret_cast<float4 *>(g);
-  float4 *m4 = reinterpret_cast<float4 *>(m), *v4 = reinterpret_cast<float4 *>(v);
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const float4 *p4 = reinterpret_cast<const float4 *>(p), *g4 = reinterpret_cast<const float4 *>(g);
+  const float4 *m4 = reinterpret_cast<const float4 *>(m), *v4 = reinterpret_cast<const float4 *>(v);
+  float4 *po = reinterpret_cast<float4 *>(p), *go = reinterpret_cast<float4 *>(g);
+  float4 *mo = reinterpret_cast<float4 *>(m), *vo = reinterpret_cast<float4 *>(v);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   auto upd = [&](float &pp, float gg, float &mm, float &vv) {
     gg += hp.l2 * pp;
     mm = hp.b1 * mm + (1.f - hp.b1) * gg;
     vv = hp.b2 * vv + (1.f - hp.b2) * gg * gg;
-    float mh = mm * inv_bc1, vh = vv * inv_bc2;
+    const float mh = mm * inv_bc1, vh = vv * inv_bc2;
     pp -= hp.lr * mh / (sqrtf(vh) + hp.eps);
   };
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-    float4 gg = __ldcs(g4 + i);
-    __stcs(g4 + i, zero);
-    if (skip) continue;
-    float4 pp = __ldcs(p4 + i), mm = __ldcs(m4 + i), vv = __ldcs(v4 + i);
-    upd(pp.x, gg.x, mm.x, vv.x);
-    upd(pp.y, gg.y, mm.y, vv.y);
-    upd(pp.z, gg.z, mm.z, vv.z);
-    upd(pp.w, gg.w, mm.w, vv.w);
-    p4[i] = pp;
-    __stcs(m4 + i, mm);
-    __stcs(v4 + i, vv);
-    if (SHADOW == 1) {
-      __half2 a = __floats2half2_rn(pp.x, pp.y), b = __floats2half2_rn(pp.z, pp.w);
-      uint2 u;
-      u.x = *reinterpret_cast<uint32_t *>(&a);
-      u.y = *reinterpret_cast<uint32_t *>(&b);
-      reinterpret_cast<uint2 *>(shadow)[i] = u;
-    } else if (SHADOW == 2) {
-      __nv_bfloat162 a = __floats2bfloat162_rn(pp.x, pp.y), b = __floats2bfloat162_rn(pp.z, pp.w);
-      uint2 u;
-      u.x = *reinterpret_cast<uint32_t *>(&a);
-      u.y = *reinterpret_cast<uint32_t *>(&b);
-      reinterpret_cast<uint2 *>(shadow)[i] = u;
+  if (skip) {  // an overflowed step: only clear the gradient
+    for (int64_t i = t0; i < n4; i += nthr) go[i] = zero;
+    for (int64_t i = (n4 << 2) + t0; i < n; i += nthr) g[i] = 0.f;
+    return;
+  }
+  // kU float4 of each of p, g, m, v are loaded before anything is stored
+  for (int64_t base = t0; base < n4; base += nthr * kU) {
+    float4 gg[kU], pp[kU], mm[kU], vv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = base + u * nthr;
+      if (i < n4) {
+        gg[u] = __ldcs(g4 + i);
+        pp[u] = __ldcs(p4 + i);
+        mm[u] = __ldcs(m4 + i);
+        vv[u] = __ldcs(v4 + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = base + u * nthr;
+      if (i < n4) {
+        upd(pp[u].x, gg[u].x, mm[u].x, vv[u].x);
+        upd(pp[u].y, gg[u].y, mm[u].y, vv[u].y);
+        upd(pp[u].z, gg[u].z, mm[u].z, vv[u].z);
+        upd(pp[u].w, gg[u].w, mm[u].w, vv[u].w);
+        __stcs(go + i, zero);
+        po[i] = pp[u];
+        __stcs(mo + i, mm[u]);
+        __stcs(vo + i, vv[u]);
+        put_shadow<SHADOW>(shadow, i, pp[u]);
+      }
     }
   }
   // tail (n not a multiple of 4)
-  for (int64_t i = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  for (int64_t i = (n4 << 2) + t0; i < n; i += nthr) {
     float gg = g[i];
     g[i] = 0.f;
-    if (skip) continue;
     float pp = p[i], mm = m[i], vv = v[i];
     upd(pp, gg, mm, vv);
-    p[i] = pp; m[i] = mm; v[i] = vv;
+    p[i] = pp;
+    m[i] = mm;
+    v[i] = vv;
     if (SHADOW == 1) reinterpret_cast<__half *>(shadow)[i] = __float2half_rn(pp);
     else if (SHADOW == 2) reinterpret_cast<__nv_bfloat16 *>(shadow)[i] = __float2bfloat16_rn(pp);
   }
@@ -111,8 +142,12 @@ __global__ void k_shadow(const float *__restrict__ p, void *__restrict__ shadow,
 nv_status launch_adam(nv_ctx *c) {
   AdamHP hp{c->adam.lr, c->adam.beta1, c->adam.beta2, c->adam.eps, c->adam.l2_reg};
   int64_t n = c->n_params;
-  int64_t want = ((n >> 2) + 255) / 256;
-  int64_t grid = (int64_t)c->num_sms * 8;
+  // one wave of resident CTAs: each thread walks the vector grid-stride
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adam<0>, 256, 0);
+  if (per_sm < 1) per_sm = 1;
+  int64_t want = ((n >> 2) / kU + 255) / 256;
+  int64_t grid = (int64_t)c->num_sms * per_sm;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
   switch (c->prec) {

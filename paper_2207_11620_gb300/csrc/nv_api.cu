@@ -85,6 +85,8 @@ static void ctx_free(nv_ctx *c) {
   cudaFree(c->shadow);
   cudaFree(c->ds);
   cudaFree(c->batch);
+  cudaFree(c->tc_feat);
+  cudaFree(c->tc_df);
   delete c;
 }
 

@@ -53,6 +53,9 @@ struct nv_ctx {
   int64_t batch_cap;
   int num_sms;
   struct Prof *prof;                        // kernel timing (nv_profile_enable), NULL when off
+  uint8_t *tc_feat;                         // tensor-core path: one chunk of 16-bit features (tile layout)
+  float *tc_df;                             // tensor-core path: one chunk of input gradients
+  int64_t tc_cap;                           // points per chunk of the two above
 };
 
 // Kernel timing hooks (nv_api.cu): bracket a launch on the context stream.

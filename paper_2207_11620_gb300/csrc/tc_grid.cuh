@@ -1,0 +1,238 @@
+// tc_grid.cuh -- device pieces shared by the tensor-core path's kernels: the
+// source of a work item's point, the chunk a launch covers, the tensor-core
+// tile layout of features in memory, 16-bit packing, and the x-paired hash
+// gather (A-1..A-3) and scatter (A-7).
+#pragma once
+
+#include "nv_internal.cuh"
+
+// Where the points of a launch come from.
+struct PointSrc {
+  const float *xyz;   // kind 0: [n][3]
+  int kind;           // 0: xyz array, 1: voxel centres of vol, 2: Philox training sample
+  nv_volume vol;      // kind 1 and the training target of kind 2
+  uint64_t seed;      // kind 2
+  uint32_t step;      // kind 2
+};
+
+__device__ __forceinline__ float3 point_at(const PointSrc &s, int64_t p) {
+  if (s.kind == 0) return make_float3(s.xyz[3 * p], s.xyz[3 * p + 1], s.xyz[3 * p + 2]);
+  if (s.kind == 1) {
+    const int64_t nx = s.vol.nx, ny = s.vol.ny;
+    const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / (nx * ny));
+    return make_float3(__fdiv_rn(__fadd_rn((float)ix, 0.5f), (float)s.vol.nx),
+                       __fdiv_rn(__fadd_rn((float)iy, 0.5f), (float)s.vol.ny),
+                       __fdiv_rn(__fadd_rn((float)iz, 0.5f), (float)s.vol.nz));
+  }
+  return nv_sample_point(s.seed, s.step, (uint64_t)p);
+}
+
+// The points [off, off + cap) of a launch; the total is n_host, or read on the
+// device as *n_dev * n_mult (the live samples of a render iteration).
+struct ChunkSpan {
+  const int *n_dev;
+  int n_mult;
+  int64_t n_host;
+  int64_t off;
+  int64_t cap;
+};
+
+__device__ __forceinline__ int64_t chunk_count(const ChunkSpan &c) {
+  const int64_t tot = c.n_dev ? (int64_t)(*c.n_dev) * c.n_mult : c.n_host;
+  int64_t n = tot - c.off;
+  if (n < 0) n = 0;
+  if (n > c.cap) n = c.cap;
+  return n;
+}
+
+// Byte offset of element (r, k) of a [rows][K] 16-bit operand stored as
+// no-swizzle core matrices: 8 rows x 16 B blocks, K-chunks adjacent, 8-row
+// groups K * 16 B apart.
+__host__ __device__ __forceinline__ uint32_t tile_off(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+template <bool BF>
+struct Half;
+template <>
+struct Half<false> {
+  using T = __half;
+  using T2 = __half2;
+  static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2half2_rn(a, b); }
+  static __device__ __forceinline__ float2 unpack(T2 v) { return __half22float2(v); }
+  static __device__ __forceinline__ float lo(T v) { return __half2float(v); }
+};
+template <>
+struct Half<true> {
+  using T = __nv_bfloat16;
+  using T2 = __nv_bfloat162;
+  static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+  static __device__ __forceinline__ float2 unpack(T2 v) { return __bfloat1622float2(v); }
+  static __device__ __forceinline__ float lo(T v) { return __bfloat162float(v); }
+};
+
+template <bool BF>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  typename Half<BF>::T2 h = Half<BF>::pack(a, b);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+template <bool BF>
+__device__ __forceinline__ uint32_t pack16x2(float a, float b) {
+  typename Half<BF>::T2 h = Half<BF>::pack(a, b);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+template <int F>
+struct Raw;  // raw 16-bit storage of one entry (single) and of two adjacent entries (pair)
+template <>
+struct Raw<1> {
+  using S = uint16_t;
+  using P = uint32_t;
+};
+template <>
+struct Raw<2> {
+  using S = uint32_t;
+  using P = uint2;
+};
+template <>
+struct Raw<4> {
+  using S = uint2;
+  using P = uint4;
+};
+
+template <int F, bool BF, typename T>
+__device__ __forceinline__ void unpack16(const T &u, float *e) {
+  using T2 = typename Half<BF>::T2;
+  const uint16_t *h = reinterpret_cast<const uint16_t *>(&u);
+  constexpr int n = (int)(sizeof(T) / 2);
+  if constexpr (n == 1) {
+    typename Half<BF>::T v = *reinterpret_cast<const typename Half<BF>::T *>(h);
+    e[0] = Half<BF>::lo(v);
+  } else {
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      float2 f = Half<BF>::unpack(*reinterpret_cast<const T2 *>(h + 2 * i));
+      e[2 * i] = f.x;
+      e[2 * i + 1] = f.y;
+    }
+  }
+}
+
+// A-1..A-3 for G consecutive levels, x-paired: corners (cx, .) and (cx + 1, .)
+// hash to entries h and h ^ 1 when cx is even (the x prime is 1), so one
+// aligned 2-entry load serves both; for odd cx the second corner is loaded
+// alone.  Every load of the G levels is issued before any is consumed, so a
+// thread waits for one memory round trip per G levels.
+template <int F, bool BF, int G>
+__device__ __forceinline__ void gather_levels(const uint16_t *__restrict__ shadow, const NetDesc &nd, int l0,
+                                              float x, float y, float z, float *out) {
+  using PT = typename Raw<F>::P;
+  using ST = typename Raw<F>::S;
+  const uint32_t mask = nd.T - 1;
+  PT pr[G][4];
+  ST sg[G][4];
+  uint32_t odd0 = 0, evenm = 0;
+  float wxs[G], wyzs[G][4];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int l = l0 + g;
+    int cx, cy, cz;
+    float wy, wz;
+    const float N = (float)nd.res[l];
+    nv_cell(x, N, cx, wxs[g]);
+    nv_cell(y, N, cy, wy);
+    nv_cell(z, N, cz, wz);
+    const bool even = (cx & 1) == 0;
+    if (even) evenm |= 1u << g;
+    const uint16_t *tab = shadow + (size_t)l * nd.T * F;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dy = q & 1, dz = q >> 1;
+      wyzs[g][q] = (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
+      const uint32_t hy = ((uint32_t)(cy + dy) * 2654435761u) ^ ((uint32_t)(cz + dz) * 805459861u);
+      const uint32_t h0 = ((uint32_t)cx ^ hy) & mask;
+      if (h0 & 1u) odd0 |= 1u << (g * 4 + q);
+      pr[g][q] = __ldg(reinterpret_cast<const PT *>(tab + (size_t)(h0 & ~1u) * F));
+      if (!even) {
+        const uint32_t h1 = ((uint32_t)(cx + 1) ^ hy) & mask;
+        sg[g][q] = __ldg(reinterpret_cast<const ST *>(tab + (size_t)h1 * F));
+      }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    float acc[F];
+#pragma unroll
+    for (int j = 0; j < F; ++j) acc[j] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float pv[2 * F], e1[F];
+      unpack16<F, BF>(pr[g][q], pv);
+      const int o0 = ((odd0 >> (g * 4 + q)) & 1u) ? F : 0;
+      if ((evenm >> g) & 1u) {
+#pragma unroll
+        for (int j = 0; j < F; ++j) e1[j] = pv[F - o0 + j];
+      } else {
+        unpack16<F, BF>(sg[g][q], e1);
+      }
+      const float w0 = (1.f - wxs[g]) * wyzs[g][q], w1 = wxs[g] * wyzs[g][q];
+#pragma unroll
+      for (int j = 0; j < F; ++j) acc[j] += w0 * pv[o0 + j] + w1 * e1[j];
+    }
+#pragma unroll
+    for (int j = 0; j < F; ++j) out[g * F + j] = acc[j];
+  }
+}
+
+template <int F>
+__device__ __forceinline__ void red_entry(float *p, const float *g) {
+  if constexpr (F == 1) {
+    atomicAdd(p, g[0]);
+  } else if constexpr (F == 2) {
+    atomicAdd(reinterpret_cast<float2 *>(p), make_float2(g[0], g[1]));
+  } else if constexpr (F == 4) {
+    atomicAdd(reinterpret_cast<float4 *>(p), make_float4(g[0], g[1], g[2], g[3]));
+  } else {
+    atomicAdd(reinterpret_cast<float4 *>(p), make_float4(g[0], g[1], g[2], g[3]));
+    atomicAdd(reinterpret_cast<float4 *>(p) + 1, make_float4(g[4], g[5], g[6], g[7]));
+  }
+}
+
+// A-7 for one level, x-paired like the gather: for even cx and F = 2 both
+// x-corners land in one 16-byte aligned pair of FP32 entries and take one
+// vector atomic.
+template <int F>
+__device__ __forceinline__ void scatter_level(float *gt, uint32_t mask, float N, float x, float y, float z,
+                                              const float *df) {
+  int cx, cy, cz;
+  float wx, wy, wz;
+  nv_cell(x, N, cx, wx);
+  nv_cell(y, N, cy, wy);
+  nv_cell(z, N, cz, wz);
+  const bool even = (cx & 1) == 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int dy = q & 1, dz = q >> 1;
+    const float wyz = (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
+    const uint32_t hy = ((uint32_t)(cy + dy) * 2654435761u) ^ ((uint32_t)(cz + dz) * 805459861u);
+    const uint32_t h0 = ((uint32_t)cx ^ hy) & mask;
+    const float w0 = (1.f - wx) * wyz, w1 = wx * wyz;
+    float g0[F], g1[F];
+#pragma unroll
+    for (int j = 0; j < F; ++j) {
+      g0[j] = w0 * df[j];
+      g1[j] = w1 * df[j];
+    }
+    if (F == 2 && even) {
+      const bool odd0 = (h0 & 1u) != 0;
+      float4 v = odd0 ? make_float4(g1[0], g1[1], g0[0], g0[1]) : make_float4(g0[0], g0[1], g1[0], g1[1]);
+      atomicAdd(reinterpret_cast<float4 *>(gt + (size_t)(h0 & ~1u) * 2), v);
+    } else {
+      const uint32_t h1 = ((uint32_t)(cx + 1) ^ hy) & mask;
+      red_entry<F>(gt + (size_t)h0 * F, g0);
+      red_entry<F>(gt + (size_t)h1 * F, g1);
+    }
+  }
+}
+

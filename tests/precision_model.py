@@ -1,0 +1,59 @@
+"""FP64 emulation of the rounding points of the tensor-core MLP (FP16 / BF16
+operands, FP32-or-better accumulation), used to derive the gradient
+tolerances of the tensor-core path from the arithmetic.
+
+The kernel rounds to the 16-bit type exactly where this model does: the
+gathered table entries and the features, the weights W0 and W1, h1, dZ2 and dZ1;
+everything else (accumulations, the output layer, the sigmoid, dF and the
+weight gradients) stays in FP32 on the GPU and in FP64 here.
+"""
+import numpy as np
+
+import oracle as O
+
+
+def round_fp16(a):
+    return np.asarray(a, np.float64).astype(np.float16).astype(np.float64)
+
+
+def round_bf16(a):
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16  # round to nearest even
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+ROUND = {"fp16": round_fp16, "bf16": round_bf16, "exact": lambda a: np.asarray(a, np.float64)}
+
+
+def backward_model(net: O.Net, params, xyz, dy, prec, scale=128.0):
+    """Per-point input gradient dF and the weight gradients (dW0, dW1, dW2) of a
+    two-hidden-layer network, with the kernel's rounding points for `prec`."""
+    rnd = ROUND[prec]
+    p = np.asarray(params, np.float64).copy()
+    p[: net.n_table] = rnd(p[: net.n_table])
+    d = net.dims
+    W = p[net.n_table:]
+    W0 = W[: d[1] * d[0]].reshape(d[1], d[0])
+    W1 = W[d[1] * d[0]: d[1] * d[0] + d[2] * d[1]].reshape(d[2], d[1])
+    W2 = W[-d[2]:]
+    f = rnd(O.encode(net, p, xyz))
+    z1 = f @ rnd(W0).T
+    h1 = rnd(np.maximum(z1, 0))
+    z2 = h1 @ rnd(W1).T
+    h2 = np.maximum(z2, 0)
+    y = 1 / (1 + np.exp(-(h2 @ W2)))
+    dz3 = np.asarray(dy, np.float64) * scale * y * (1 - y)
+    dZ2 = rnd((dz3[:, None] * W2[None, :]) * (z2 > 0))
+    dZ1 = rnd((dZ2 @ rnd(W1)) * (z1 > 0))
+    dF = (dZ1 @ rnd(W0)) / scale
+    return dF, (dZ1.T @ f) / scale, (dZ2.T @ h1) / scale, (dz3 @ h2) / scale
+
+
+def normwise(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def expected_errors(net, params, xyz, dy, prec):
+    exact = backward_model(net, params, xyz, dy, "exact")
+    got = backward_model(net, params, xyz, dy, prec)
+    return {name: normwise(g, e) for name, g, e in zip(("dF", "dW0", "dW1", "dW2"), got, exact)}

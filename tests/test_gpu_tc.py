@@ -10,8 +10,13 @@ times that.  The upstream gradients of these checks have one sign, so the
 batch sums do not cancel: with mixed signs a sum shrinks to ~sqrt(n) of its
 terms and the ReLU decisions that the FP16 forward flips near z = 0 (a
 ~1e-3 fraction) then show up as a ~sqrt(1e-3) relative error that says
-nothing about the arithmetic.  The full training step, which uses the L2
-gradient as it comes, is checked through the Adam step it produces.
+nothing about the arithmetic.  The table gradient is a scatter of the
+per-point input gradient dF, which no batch sum averages: the ReLU decisions
+flipped by the rounded forward stay in it, so its bound (TABLE_TOL) is set from
+an FP64 emulation of the kernel's rounding points (tests/precision_model.py,
+checked by tests/test_precision_model.py: 2.3% FP16, 5.7% BF16 on config 2).
+The full training step, which uses the L2 gradient as it comes, is checked
+through the Adam step it produces.
 """
 import numpy as np
 import pytest
@@ -24,7 +29,8 @@ from paper_2207_11620_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 OUT_TOL = 2e-2
-GRAD_TOL = {"fp16": 2e-2, "bf16": 5e-2}
+GRAD_TOL = {"fp16": 2e-2, "bf16": 5e-2}     # weight gradients (batch sums)
+TABLE_TOL = {"fp16": 4e-2, "bf16": 1e-1}    # table gradients (per-point dF, scattered)
 
 
 @pytest.fixture(scope="module")
@@ -100,7 +106,7 @@ def test_tc_backward_matches_oracle(nv, prec, shape):
     for k in range(len(d) - 1):
         sl = slice(nt + offs[k], nt + offs[k + 1])
         assert norm_rel(got[sl], want[sl]) <= tol, (k, norm_rel(got[sl], want[sl]))
-    assert norm_rel(got[:nt], want[:nt]) <= tol, norm_rel(got[:nt], want[:nt])
+    assert norm_rel(got[:nt], want[:nt]) <= TABLE_TOL[prec], norm_rel(got[:nt], want[:nt])
     assert np.all(got[:nt][want[:nt] == 0] == 0)
 
 
