@@ -192,6 +192,32 @@ nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_
 /* Iterations and samples of the last nv_render (synchronises). */
 nv_status nv_render_stats(nv_renderer *r, int *iterations, int64_t *samples);
 
+/* The paper has no counterpart to this entry point.  It is nv_render on the
+ * raw volume (net = NULL) for callers that cannot allocate device memory: code
+ * running while a CUDA graph is captured on its stream, real-time loops whose
+ * memory is fixed up front, or plugins inside an application that owns every
+ * allocation.  It calls no cudaMalloc, cudaFree, cudaMallocHost, event or
+ * stream creation; ray buffers, sample batches and counters come from one
+ * static device array of NV_NOALLOC_SCRATCH_BYTES (about 16 MB) that every GPU
+ * loading the library holds until the process exits.
+ *  - Images up to NV_NOALLOC_MAX_PIXELS pixels (256 x 256) and K up to
+ *    NV_NOALLOC_MAX_K; larger requests fail with NV_ERR_ARG and a message.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array and it keeps the last call's contents; each
+ *    call clears the counters that must start at zero.  Calls whose GPU work
+ *    overlaps (other streams, other host threads) race on the same scratch.
+ *  - The live-ray count is read back synchronously after every iteration, so
+ *    the call returns when the image is complete.
+ * Arguments as nv_render; mc may be NULL; stream NULL = legacy default stream. */
+#define NV_NOALLOC_MAX_PIXELS 65536
+#define NV_NOALLOC_MAX_K 8
+#define NV_NOALLOC_SCRATCH_BYTES 15991296
+nv_status nv_render_raw_noalloc(const nv_volume *raw, const nv_camera *cam, const float *lut_dev,
+                                const nv_macrocells *mc, const nv_render_opts *opts, float *rgba_dev,
+                                void *stream);
+
 /* ---- quality (Sec. 7) ------------------------------------------------------ */
 
 /* A-16: FP64 mean squared error over the RGB channels of two images,

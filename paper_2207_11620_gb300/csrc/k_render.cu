@@ -410,3 +410,58 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   for (int j = 0; j < R; ++j) cudaEventDestroy(ev[j]);
   return s;
 }
+
+// The ray march of render_impl on the raw volume, for scratch the caller
+// provides in `r` (ray buffers, sample batches, counters) and without any host
+// allocation: no events and no pinned buffer -- the live count of each
+// iteration is copied into a host stack variable and the stream synchronised.
+nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const nv_camera &cam, const float *lut,
+                               const nv_macrocells *mc, const nv_render_opts &o, float *rgba, cudaStream_t st) {
+  const int64_t npix = (int64_t)cam.width * cam.height;
+  const int64_t cap = r.max_pixels;
+  const int K = r.K;
+  cudaError_t e = cudaMemsetAsync(r.counters, 0, 2 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(r.d_samples, 0, sizeof(int64_t), st);
+  if (e != cudaSuccess) return nv_cuda_check(e, "render memset");
+  float4 *out = reinterpret_cast<float4 *>(rgba);
+  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r.ray[0], r.next_k[0], cap, &r.counters[0], out);
+  nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
+  if (s != NV_OK) return s;
+  McView mv{nullptr, 1, 1, 1, 0.f, 0.f, 0.f};
+  if (mc) {
+    mv.mu = mc->mu_max_dev;
+    mv.ncx = (mc->nx + mc->cell - 1) / mc->cell;
+    mv.ncy = (mc->ny + mc->cell - 1) / mc->cell;
+    mv.ncz = (mc->nz + mc->cell - 1) / mc->cell;
+    mv.sx = (float)mc->nx / (float)mc->cell;
+    mv.sy = (float)mc->ny / (float)mc->cell;
+    mv.sz = (float)mc->nz / (float)mc->cell;
+  }
+  const int64_t max_iter = (int64_t)std::ceil(1.7320509 / (double)o.step / (double)K) + 4;
+  int live = 0;
+  if ((e = cudaMemcpyAsync(&live, &r.counters[0], sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return nv_cuda_check(e, "render live count");
+  int cur = 0;
+  for (int64_t it = 0; live > 0; ++it) {
+    if (it >= max_iter) return nv_fail(NV_ERR_STATE, "ray march did not finish within %lld iterations", (long long)max_iter);
+    const int nxt = cur ^ 1;
+    const int64_t bound = live;
+    k_coords<<<blocks_for(bound, 128), 128, 0, st>>>(r.ray[cur], r.next_k[cur], cap, &r.counters[cur], K, o.step, mv,
+                                                     r.coords, r.nvalid);
+    if ((s = nv_cuda_check(cudaGetLastError(), "k_coords launch")) != NV_OK) return s;
+    k_values_raw<<<blocks_for(bound * K, 256), 256, 0, st>>>(raw, r.coords, &r.counters[cur], K, r.values);
+    if ((s = nv_cuda_check(cudaGetLastError(), "k_values_raw launch")) != NV_OK) return s;
+    if ((e = cudaMemsetAsync(&r.counters[nxt], 0, sizeof(int), st)) != cudaSuccess)
+      return nv_cuda_check(e, "cudaMemsetAsync");
+    k_composite<<<blocks_for(bound, 128), 128, 0, st>>>(
+        r.ray[cur], r.next_k[cur], cap, &r.counters[cur], r.values, r.nvalid, K, lut, o.alpha_exp, o.et, r.ray[nxt],
+        r.next_k[nxt], &r.counters[nxt], out, reinterpret_cast<unsigned long long *>(r.d_samples));
+    if ((s = nv_cuda_check(cudaGetLastError(), "k_composite launch")) != NV_OK) return s;
+    if ((e = cudaMemcpyAsync(&live, &r.counters[nxt], sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return nv_cuda_check(e, "render live count");
+    cur = nxt;
+  }
+  return NV_OK;
+}

@@ -80,6 +80,8 @@ EXPORTS = {
     "nv_render": ([C.c_void_p, C.c_void_p, C.POINTER(Volume), C.POINTER(Camera), C.c_void_p,
                    C.POINTER(Macrocells), C.POINTER(RenderOpts), C.c_void_p], C.c_int),
     "nv_render_stats": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64)], C.c_int),
+    "nv_render_raw_noalloc": ([C.POINTER(Volume), C.POINTER(Camera), C.c_void_p, C.POINTER(Macrocells),
+                               C.POINTER(RenderOpts), C.c_void_p, C.c_void_p], C.c_int),
     "nv_image_mse": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "nv_volume_mse": ([C.c_void_p, C.POINTER(Volume), C.c_void_p], C.c_int),
     "nv_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
