@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "fp16", "bf16"])
     ap.add_argument("--cpu-points", type=int, default=32768, help="oracle sample size (points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="", choices=["", "render1080p"],
+                    help="run one profiling case instead of the benchmark")
     ap.add_argument("--extras", default="cfg2_quality,cfg3_render,cfg4_inloop",
                     help="comma list of extra measurements (empty for none)")
     return ap.parse_args()
@@ -192,6 +194,67 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ roofline ---
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic_cfg2.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        f = line.split("#", 1)[0].split()
+        if len(f) == 2 and f[0] == kernel:
+            return int(f[1])
+    return None
+
+
+def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d):
+    """Roofline of one kernel of the config-2 step from its live average launch time.
+
+    Algorithmic bytes / FLOPs per launch (per unit x units):
+      adam     34 B per parameter (read p, g, m, v; write p, m, v, g = 0, 16-bit shadow); 32 in FP32
+      scatter  dF read (4 D0 B per point) + the FP32 table gradient read and written once (8 B per entry)
+      encode   the 16-bit table shadow read once (2 B per entry) + 16-bit features written (2 D0 B per point)
+      mlp      tensor-core FLOPs per point: 2 (D0 64 + 64 64) forward + 2 (2 64 64 + 2 64 D0) backward;
+               FP32 path: the same products plus the output layer on CUDA cores"""
+    ms = avg[kind]
+    D0 = d[0]
+    if kind == "adam":
+        unit = n_params
+        bytes_ = n_params * (32 + (2 if prec != "fp32" else 0))
+        name = "k_adam"
+    elif kind == "scatter":
+        bytes_ = batch * D0 * 4 + n_table * 8
+        name = "k_scatter_tiles"
+    elif kind == "encode":
+        bytes_ = n_table * 2 + batch * D0 * 2
+        name = "k_encode_tiles"
+    else:
+        bytes_ = None
+        name = "k_mlp_tc" if prec != "fp32" else "k_mlp_f32"
+    if bytes_ is not None:
+        ach = bytes_ / (ms / 1e3) / 1e9
+        r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+             "frac": ach / pk["hbm_gbs"], "traffic": ncu_traffic(name), "peak_kind": pk_kind + " (copy)",
+             "algorithmic_bytes_per_launch": bytes_, "avg_ms": ms}
+        if kind in ("scatter", "encode"):
+            r["limiter"] = ("L2: scattered 32-byte sector requests (gathers) / vector reductions (scatter), "
+                            "not DRAM bytes; see profiles/tc_train_kernels_cfg2.md")
+        return r
+    flops = 2 * batch * (D0 * 64 + 64 * 64) + 2 * batch * (2 * 64 * 64 + 2 * 64 * D0)
+    ach = flops / (ms / 1e3) / 1e12
+    if prec == "fp32":
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
+                "algorithmic_flops_per_launch": flops, "avg_ms": ms}
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": ncu_traffic(name), "peak_kind": pk_kind + " (bf16 sustained)",
+            "algorithmic_flops_per_launch": flops, "avg_ms": ms}
+
+
 # ---------------------------------------------------------------------- ours ---
 
 def run_ours(args):
@@ -232,7 +295,8 @@ def run_ours(args):
     clocks = Clocks(local)
     clocks.start()
     net.profile(True)
-    net.profile_read("mlp"), net.profile_read("adam"), net.profile_read("finish")
+    for k in ("mlp", "adam", "finish", "encode", "scatter"):
+        net.profile_read(k)
     barrier(ws)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -282,34 +346,14 @@ def run_ours(args):
     if rank != 0:
         return 0
     pk, pk_kind = peaks()
-    mlp_avg = k_mlp[0] / max(1, k_mlp[1])
-    adam_avg = k_adam[0] / max(1, k_adam[1])
-    n_params = net.n_params
-    shadow = 2 if prec != "fp32" else 0
-    adam_bytes = n_params * (32 + shadow)
-    if k_adam[0] >= k_mlp[0]:
-        ach = adam_bytes / (adam_avg / 1e3) / 1e9
-        roof = {"kernel": "k_adam", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind,
-                "algorithmic_bytes_per_launch": adam_bytes, "avg_ms": adam_avg}
-    else:
-        # fused sample + encode + MLP forward/backward: count only the MLP MACs
-        d = c.dims
-        fwd = sum(d[k] * d[k + 1] for k in range(len(d) - 1))
-        bwd_x = sum(d[k] * d[k + 1] for k in range(len(d) - 1))
-        flops = 2 * batch * (fwd + bwd_x + fwd)
-        ach = flops / (mlp_avg / 1e3) / 1e12
-        if prec == "fp32":
-            peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            roof = {"kernel": "k_mlp_f32<TRAIN>", "bound": "alu", "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                    "algorithmic_flops_per_launch": flops, "avg_ms": mlp_avg}
-        else:
-            peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-            roof = {"kernel": "k_mlp_tc<TRAIN>", "bound": "tensor", "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_kind": pk_kind,
-                    "algorithmic_flops_per_launch": flops, "avg_ms": mlp_avg}
+    kt = {k: net.profile_read(k) for k in ("encode", "scatter")}
+    kt["mlp"], kt["adam"], kt["finish"] = k_mlp, k_adam, k_fin
+    avg = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in kt.items()}
+    n_params, n_table = net.n_params, net.n_table
+    d = c.dims
+    D0 = d[0]
+    roof = roofline_of(max(("encode", "mlp", "scatter", "adam"), key=lambda k: kt[k][0]), avg, prec, pk, pk_kind,
+                       batch, n_params, n_table, d)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -320,10 +364,9 @@ def run_ours(args):
                    "l2": "working set > L2: each step's Adam streams params, grads, m, v (269 MB)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
-        "kernels_ms_per_step": {"mlp_fused": mlp_avg, "adam": adam_avg,
-                                "finish": k_fin[0] / max(1, k_fin[1])},
+        "kernels_ms_per_step": {k: v for k, v in avg.items() if v > 0},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": batch * 16, "d2h_bytes_per_step": 8},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": args.steps * sum(1 for k in ("encode", "mlp", "scatter", "adam", "finish") if kt[k][1]),
         "clocks": clk,
     }
     if ws == 1 and args.extras:
@@ -486,8 +529,38 @@ def run_extras(args):
     return out
 
 
+def run_case(args):
+    """Profiling case (for ncu captures): two 1080p frames of the config-3 geometry
+    with a random-weight FP16 network; prints one JSON line."""
+    import torch
+    from paper_2207_11620_gb300 import build as B
+    from paper_2207_11620_gb300 import configs as CF
+    from paper_2207_11620_gb300 import inputs as I
+    from paper_2207_11620_gb300 import nv
+    B.build()
+    cfg = CF.CFG3
+    c = cfg["net"]
+    D = cfg["volume"]
+    vt = I.blob_volume_torch(D, cfg["volume_seed"], "cuda")
+    lut, mu, opts = _render_setup(nv, I, torch, cfg, vt)
+    net = nv.NeuralVolume(prec="fp16", **c.kwargs())
+    p = I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims)
+    p[: net.n_table] = I.uniform_params(net.n_table, seed=6, scale=0.5)
+    net.set_params(p)
+    W, H = cfg["image"]
+    cam = I.perspective_camera(W, H, cfg["vfov"], cfg["eye"], cfg["target"])
+    r = nv.Renderer(W * H, K=cfg["K"])
+    img, ms = _time_render(r, torch, 1, cam=cam, lut=lut, opts=opts, net=net, mc=(mu, cfg["cell"], vt.shape))
+    it, ns = r.stats()
+    print(json.dumps({"case": args.case, "frame_ms": ms, "iterations": it, "samples": ns,
+                      "mean_alpha": float(img[..., 3].mean())}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

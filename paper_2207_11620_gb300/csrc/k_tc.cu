@@ -600,13 +600,19 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
   const bool bwd = mode == MODE_TRAIN || mode == MODE_BACKWARD;
   for (int64_t off = 0; off < n_upper; off += c->tc_cap) {
     ChunkSpan cs{n_dev, n_mult, a.n, off, n_upper - off < c->tc_cap ? n_upper - off : c->tc_cap};
+    int tk = prof_begin(c);
     s = launch_encode_tiles(c, ps, cs, c->tc_feat);
+    prof_end(c, NV_K_ENCODE, tk);
     if (s != NV_OK) return s;
+    tk = prof_begin(c);
     s = c->prec == NV_BF16 ? dispatch_shape<true>(c, mode, a, ps, cs, c->tc_feat, c->tc_df, acc)
                            : dispatch_shape<false>(c, mode, a, ps, cs, c->tc_feat, c->tc_df, acc);
+    prof_end(c, NV_K_MLP, tk);
     if (s != NV_OK) return s;
     if (bwd) {
+      tk = prof_begin(c);
       s = launch_scatter_tiles(c, ps, cs, c->tc_df, a.grads);
+      prof_end(c, NV_K_SCATTER, tk);
       if (s != NV_OK) return s;
     }
   }

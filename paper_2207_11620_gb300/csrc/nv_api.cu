@@ -278,8 +278,9 @@ extern "C" nv_status nv_infer(nv_ctx *c, const float *xyz, int64_t n, float *y) 
   a.n = n;
   a.y = y;
   a.ds = c->ds;
+  if (c->prec != NV_FP32) return launch_mlp_tc(c, MODE_INFER, a);  // times its kernels itself
   int tk = prof_begin(c);
-  nv_status s = c->prec == NV_FP32 ? launch_mlp_f32(c, MODE_INFER, a) : launch_mlp_tc(c, MODE_INFER, a);
+  nv_status s = launch_mlp_f32(c, MODE_INFER, a);
   prof_end(c, NV_K_MLP, tk);
   return s;
 }
@@ -294,8 +295,9 @@ extern "C" nv_status nv_backward(nv_ctx *c, const float *xyz, int64_t n, const f
   a.n = n;
   a.grads = dparams ? dparams : c->grads;
   a.ds = c->ds;
+  if (c->prec != NV_FP32) return launch_mlp_tc(c, MODE_BACKWARD, a);  // times its kernels itself
   int tk = prof_begin(c);
-  nv_status s = c->prec == NV_FP32 ? launch_mlp_f32(c, MODE_BACKWARD, a) : launch_mlp_tc(c, MODE_BACKWARD, a);
+  nv_status s = launch_mlp_f32(c, MODE_BACKWARD, a);
   prof_end(c, NV_K_MLP, tk);
   return s;
 }
@@ -359,10 +361,14 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
     a.seed = seed;
     a.sample_step = c->sample_counter++;
   }
+  if (c->prec == NV_FP32) {
+    int tk0 = prof_begin(c);
+    NV_TRY(launch_mlp_f32(c, MODE_TRAIN, a));
+    prof_end(c, NV_K_MLP, tk0);
+  } else {
+    NV_TRY(launch_mlp_tc(c, MODE_TRAIN, a));  // times its encode / MLP / scatter kernels itself
+  }
   int tk = prof_begin(c);
-  NV_TRY(c->prec == NV_FP32 ? launch_mlp_f32(c, MODE_TRAIN, a) : launch_mlp_tc(c, MODE_TRAIN, a));
-  prof_end(c, NV_K_MLP, tk);
-  tk = prof_begin(c);
   NV_TRY(launch_adam(c));
   prof_end(c, NV_K_ADAM, tk);
   tk = prof_begin(c);

@@ -19,7 +19,7 @@ LIB_PATH = _build.LIB
 NV_FP32, NV_FP16, NV_BF16 = 0, 1, 2
 PREC = {"fp32": NV_FP32, "fp16": NV_FP16, "bf16": NV_BF16}
 BUF = {"params": 0, "grads": 1, "adam_m": 2, "adam_v": 3}
-KCLASS = {"mlp": 0, "adam": 1, "finish": 2, "render": 3, "other": 4}
+KCLASS = {"mlp": 0, "adam": 1, "finish": 2, "render": 3, "other": 4, "encode": 5, "scatter": 6}
 
 
 class NvError(RuntimeError):
