@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default="", choices=["", "render1080p"],
                     help="run one profiling case instead of the benchmark")
-    ap.add_argument("--extras", default="cfg2_quality,cfg3_render,cfg4_inloop",
+    ap.add_argument("--extras", default="cfg2_quality,cfg3_render,cfg4_inloop,cfg5_ooc",
                     help="comma list of extra measurements (empty for none)")
     return ap.parse_args()
 
@@ -512,6 +512,66 @@ def extra_cfg4_inloop(nv, I, CF, torch, frames=None):
     return out
 
 
+def extra_cfg5_ooc(nv, I, CF, torch, steps=200, warm=10):
+    """Config 5: 2048^3 volume (32 GiB) held in pinned host memory as 64^3 bricks with
+    a ghost layer; a device ring of 4096 bricks, 256 refreshed per step on a side
+    stream; 2^19 BF16 training points per step from the resident bricks.  The
+    device copy of the volume is freed before training; the final PSNR is taken
+    on a 256^3 subsample (every 8th voxel) kept on the device."""
+    cfg = CF.CFG5
+    c = cfg["net"]
+    D, B = cfg["volume"], cfg["brick"]
+    t0 = time.perf_counter()
+    vt = I.blob_volume_torch(D, cfg["volume_seed"], "cuda")
+    sub = vt[4::8, 4::8, 4::8].contiguous().reshape(-1)
+    ax = (torch.arange(4, D, 8, device="cuda", dtype=torch.float32) + 0.5) / D
+    zz, yy, xx = torch.meshgrid(ax, ax, ax, indexing="ij")
+    pts = torch.stack([xx, yy, zz], -1).reshape(-1, 3).contiguous()
+    del zz, yy, xx
+    host = I.host_bricks_from_device(vt, B)
+    del vt
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    prep_s = time.perf_counter() - t0
+    ring = nv.BrickRing(host, (D, D, D), B, cfg["ring"], seed=1)
+    net = nv.NeuralVolume(prec="bf16", **c.kwargs())
+    net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
+    n = cfg["batch"]
+    xyz = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    tgt = torch.empty(n, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def step(s):
+        ring.sample(n, seed=17, step=s, xyz=xyz, target=tgt)
+        ring.refresh(cfg["refresh"], seed=1000 + s)  # overlaps the training step below
+        net.train_step(xyz, tgt, loss_out=loss)
+
+    for s in range(warm):
+        step(s)
+    torch.cuda.synchronize()
+    b0, c0 = ring.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(warm, warm + steps):
+        step(s)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    b1, c1 = ring.stats()
+    y = net.infer(pts)
+    psnr = _psnr(nv.mse(y, sub).item())
+    out = {"steps": steps, "ms_per_step": ms, "steps_per_s": 1e3 / ms, "samples_per_s": n * 1e3 / ms,
+           "bytes_per_step": (b1 - b0) / steps, "host_link_gbs": (b1 - b0) / (c1 - c0) / 1e6 if c1 > c0 else None,
+           "sustained_host_gbs": (b1 - b0) / (steps * ms) / 1e6, "final_loss": loss.item(),
+           "psnr_db_256cube_subsample": psnr, "host_bytes": host.numel() * 4, "prep_s": prep_s,
+           "ring_bricks": cfg["ring"], "refresh_per_step": cfg["refresh"], "n_params": net.n_params}
+    net.close()
+    ring.close()
+    del host, pts, sub
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_extras(args):
     import torch
     from paper_2207_11620_gb300 import configs as CF
@@ -519,7 +579,7 @@ def run_extras(args):
     from paper_2207_11620_gb300 import nv
     out = {}
     for name, fn in (("cfg2_quality", extra_cfg2_quality), ("cfg3_render", extra_cfg3_render),
-                     ("cfg4_inloop", extra_cfg4_inloop)):
+                     ("cfg4_inloop", extra_cfg4_inloop), ("cfg5_ooc", extra_cfg5_ooc)):
         if name not in args.extras:
             continue
         try:

@@ -164,6 +164,41 @@ nv_status nv_sample(const nv_volume *vol, int64_t n, uint64_t seed, uint32_t ste
 nv_status nv_train_step(nv_ctx *ctx, const float *xyz_any, const float *target_any, int64_t n,
                         const nv_volume *vol, uint64_t seed, double *loss_dev);
 
+/* ---- out-of-core training samples (Sec. 4.1) ------------------------------- */
+
+/* A-17: a device ring of R bricks fed from a volume held in pinned host memory
+ * (Sec. 4.1, Fig. 2).  host_bricks: nbx*nby*nbz bricks (nb = n / brick per
+ * axis, n a multiple of brick), brick b = (bz*nby + by)*nbx + bx at offset
+ * b*(brick+2)^3 floats, each holding voxels brick*b - 1 .. brick*b + brick of
+ * its axis range (indices clamped to the volume: the ghost layer), x fastest.
+ * The memory stays owned by the caller and must outlive the ring.  Creation
+ * fills every slot (the warm-up) and waits; the ring owns a copy stream.
+ * Brick choices: splitmix64 of (seed, refresh count, slot) modulo the brick
+ * count. */
+typedef struct nv_ooc nv_ooc;
+nv_status nv_ooc_create(const float *host_bricks, int nx, int ny, int nz, int brick, int ring_slots,
+                        uint64_t seed, nv_ooc **out);
+nv_status nv_ooc_destroy(nv_ooc *ooc);
+/* Replace `count` slots (round robin) with freshly chosen bricks: a gather
+ * kernel on the ring's own high-priority stream reads them from the pinned
+ * host bricks over the host link.  It starts after the work already enqueued
+ * on `stream` (so call it right after the nv_ooc_sample that last reads the
+ * ring) and the next nv_ooc_sample waits for it; the training work enqueued in
+ * between overlaps the copies. */
+nv_status nv_ooc_refresh(nv_ooc *ooc, int count, uint64_t seed, void *stream);
+/* n training samples from the resident bricks on `stream`: slot = u0 mod R,
+ * voxel = the low three bytes of u1 mod brick, jitter (u >> 8) 2^-24 - 1/2 from
+ * u2, u3 and the next draw's u0 (Philox4x32-10, counters (i lo, i hi, step, 1)
+ * and (.., 2), key seed); position (v + 1/2 + jitter) / n; target trilinear
+ * inside the brick.  xyz_dev [n][3] and target_dev [n] may each be NULL. */
+nv_status nv_ooc_sample(nv_ooc *ooc, int64_t n, uint64_t seed, uint32_t step, float *xyz_dev,
+                        float *target_dev, void *stream);
+/* The brick held by each slot as of the last refresh (host array [R]). */
+nv_status nv_ooc_slots(nv_ooc *ooc, int *slot_brick);
+/* Bytes copied by refreshes since creation and the copy stream's busy time
+ * for them (synchronises the copy stream). */
+nv_status nv_ooc_stats(nv_ooc *ooc, int64_t *bytes_copied, double *copy_ms);
+
 /* ---- rendering (Sec. 5) --------------------------------------------------- */
 
 /* A-10: macrocells of `cell` voxels (Sec. 5.3).  minmax_dev [nc][2] holds the
@@ -224,6 +259,9 @@ nv_status nv_render_raw_noalloc(const nv_volume *raw, const nv_camera *cam, cons
  * mse_dev (one double on the device). */
 nv_status nv_image_mse(const float *rgba_a_dev, const float *rgba_b_dev, int64_t n_pixels,
                        double *mse_dev, void *stream);
+/* A-16: FP64 mean squared error of two float arrays of n values (e.g. decoded
+ * and raw values at the same points), mse_dev (one double on the device). */
+nv_status nv_mse_f64(const float *a_dev, const float *b_dev, int64_t n, double *mse_dev, void *stream);
 /* A-16: decode the network at every voxel centre (i + 1/2) / n and the FP64 MSE
  * against vol, mse_dev (one double on the device).  No decoded grid is stored. */
 nv_status nv_volume_mse(nv_ctx *ctx, const nv_volume *vol, double *mse_dev);

@@ -644,3 +644,44 @@ double or_volume_mse(int L, int F, int log2T, const int *res, const int *dims, i
   }
   return nvox > 0 ? total / (double)nvox : 0.0;
 }
+
+/* ------------------------------------------------------- out of core -- */
+
+/* Sec. 4.1 (out-of-core sampling): a training point is drawn from one of the R
+ * blocks resident in the ring: pick a slot, pick a voxel of that block, jitter
+ * the voxel centre by U[-0.5, 0.5] per axis; its target is the trilinear value
+ * of the volume there (the block's ghost layer makes that value available
+ * inside the block).  Random words: Philox4x32-10 with key (seed lo, seed hi);
+ * counter (i lo, i hi, step, 1) gives u0 (slot = u0 mod R), u1 (voxel: bits
+ * 0-7 / 8-15 / 16-23 mod B per axis), u2, u3 (x and y jitter); counter
+ * (i lo, i hi, step, 2) gives u0 (z jitter); jitter = (u >> 8) 2^-24 - 1/2.
+ * Blocks are B^3 voxels, block b = (bz nby + by) nbx + bx; slot_brick[s] is
+ * the block held by slot s.  The position is (v + 1/2 + jitter) / n per axis
+ * in FP32 (it decides the interpolation cell); the target is FP64. */
+void or_brick_sample(const float *vol, int nx, int ny, int nz, int B, const int *slot_brick, int R,
+                     uint64_t seed, uint32_t step, int64_t n, float *xyz, double *target) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  int nbx = nx / B, nby = ny / B;
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t id = (uint64_t)i;
+    uint32_t c1[4] = {(uint32_t)id, (uint32_t)(id >> 32), step, 1u}, c2[4] = {(uint32_t)id, (uint32_t)(id >> 32), step, 2u};
+    uint32_t u[4], w[4];
+    or_philox4x32_10(c1, key, u);
+    or_philox4x32_10(c2, key, w);
+    int s = (int)(u[0] % (uint32_t)R);
+    int b = slot_brick[s];
+    int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+    int v[3] = {bx * B + (int)((u[1] & 255u) % (uint32_t)B), by * B + (int)(((u[1] >> 8) & 255u) % (uint32_t)B),
+                bz * B + (int)(((u[1] >> 16) & 255u) % (uint32_t)B)};
+    uint32_t jw[3] = {u[2], u[3], w[0]};
+    int dims[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+      float j = (float)(jw[a] >> 8) * (1.0f / 16777216.0f);
+      j = j - 0.5f;
+      float p = (float)v[a] + 0.5f;
+      p = p + j;
+      xyz[3 * i + a] = p / (float)dims[a];
+    }
+    target[i] = or_trilinear_point(vol, nx, ny, nz, xyz + 3 * i);
+  }
+}

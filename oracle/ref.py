@@ -96,6 +96,8 @@ def lib():
         L.or_volume_mse.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
                                     C.c_int, C.c_int, C.c_int]
         L.or_volume_mse.restype = C.c_double
+        L.or_brick_sample.argtypes = [_f32p, C.c_int, C.c_int, C.c_int, C.c_int, _i32p, C.c_int, C.c_uint64,
+                                      C.c_uint32, C.c_int64, _f32p, _f64p]
     return _lib
 
 
@@ -338,3 +340,14 @@ def volume_mse(net: Net, params, vol):
     nz, ny, nx = vol.shape
     return float(lib().or_volume_mse(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims),
                                      _f64(params), vol, nx, ny, nz))
+
+
+def brick_sample(vol, brick, slot_brick, seed, step, n):
+    """Out-of-core training sample (Sec. 4.1): points and FP64 targets."""
+    vol = _f32(vol)
+    nz, ny, nx = vol.shape
+    sb = np.ascontiguousarray(slot_brick, dtype=np.int32)
+    xyz = np.zeros((n, 3), np.float32)
+    t = np.zeros(n, np.float64)
+    lib().or_brick_sample(vol, nx, ny, nz, int(brick), sb, len(sb), int(seed), int(step), int(n), xyz, t)
+    return xyz, t

@@ -465,3 +465,34 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
   }
   return NV_OK;
 }
+
+namespace {
+// A-16: FP64 sum of squared differences of two float arrays; each CTA adds partial / n.
+__global__ void __launch_bounds__(256) k_mse(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
+                                             double scale, double *out) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = (double)a[i] - (double)b[i];
+    s += d * d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    atomicAdd(out, t * scale);
+  }
+}
+}  // namespace
+
+nv_status launch_mse(const float *a, const float *b, int64_t n, double *out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return nv_cuda_check(e, "cudaMemsetAsync");
+  if (n == 0) return NV_OK;
+  unsigned grid = (unsigned)std::min<int64_t>(blocks_for(n, 256), 1216);
+  k_mse<<<grid, 256, 0, s>>>(a, b, n, 1.0 / (double)n, out);
+  return nv_cuda_check(cudaGetLastError(), "k_mse launch");
+}

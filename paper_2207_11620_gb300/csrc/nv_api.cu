@@ -471,6 +471,11 @@ extern "C" nv_status nv_image_mse(const float *a, const float *b, int64_t n, dou
   return launch_image_mse(a, b, n, mse, (cudaStream_t)stream);
 }
 
+extern "C" nv_status nv_mse_f64(const float *a, const float *b, int64_t n, double *mse, void *stream) {
+  if (!a || !b || !mse || n < 0) return nv_fail(NV_ERR_ARG, "nv_mse_f64: bad argument");
+  return launch_mse(a, b, n, mse, (cudaStream_t)stream);
+}
+
 extern "C" nv_status nv_volume_mse(nv_ctx *c, const nv_volume *vol, double *mse) {
   if (!c || !mse) return nv_fail(NV_ERR_ARG, "nv_volume_mse: NULL argument");
   NV_TRY(check_volume(vol, "nv_volume_mse"));

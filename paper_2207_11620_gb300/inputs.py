@@ -119,3 +119,38 @@ def perspective_camera(width: int, height: int, vfov_deg: float = 40.0,
     return dict(eye=eye, target=target, up=up,
                 tan_half_fovy=float(np.float32(np.tan(np.radians(vfov_deg) / 2.0))),
                 ortho_w=0.0, ortho_h=0.0, width=width, height=height)
+
+
+def host_bricks(vol: np.ndarray, brick: int) -> np.ndarray:
+    """Brick layout of a volume for out-of-core sampling: [nbz*nby*nbx][(B+2)^3],
+    brick (bx, by, bz) holding voxels B*b - 1 .. B*b + B per axis (indices
+    clamped to the volume: a one-voxel ghost layer), x fastest."""
+    nz, ny, nx = vol.shape
+    B = brick
+    pad = np.pad(vol, 1, mode="edge")
+    out = np.empty((nz // B, ny // B, nx // B, B + 2, B + 2, B + 2), np.float32)
+    for bz in range(nz // B):
+        for by in range(ny // B):
+            for bx in range(nx // B):
+                out[bz, by, bx] = pad[bz * B: bz * B + B + 2, by * B: by * B + B + 2, bx * B: bx * B + B + 2]
+    return out.reshape(-1, (B + 2) ** 3)
+
+
+def host_bricks_from_device(vol, brick: int):
+    """Same layout built on the GPU slab by slab from a CUDA volume into a pinned
+    CPU tensor (for volumes too large to pad on the host)."""
+    import torch
+    nz, ny, nx = vol.shape
+    B = brick
+    E = B + 2
+    out = torch.empty(((nz // B) * (ny // B) * (nx // B), E ** 3), dtype=torch.float32, pin_memory=True)
+    iy = torch.clamp(torch.arange(-1, ny + 1, device=vol.device), 0, ny - 1)
+    ix = torch.clamp(torch.arange(-1, nx + 1, device=vol.device), 0, nx - 1)
+    per_layer = (ny // B) * (nx // B)
+    for bz in range(nz // B):
+        iz = torch.clamp(torch.arange(bz * B - 1, bz * B + B + 1, device=vol.device), 0, nz - 1)
+        slab = vol.index_select(0, iz).index_select(1, iy).index_select(2, ix)  # [E][ny+2][nx+2]
+        bricks = slab.unfold(1, E, B).unfold(2, E, B)                            # [E][nby][nbx][E][E]
+        bricks = bricks.permute(1, 2, 0, 3, 4).reshape(per_layer, E ** 3)
+        out[bz * per_layer:(bz + 1) * per_layer].copy_(bricks)
+    return out

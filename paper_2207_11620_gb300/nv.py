@@ -84,6 +84,14 @@ EXPORTS = {
                                C.POINTER(RenderOpts), C.c_void_p, C.c_void_p], C.c_int),
     "nv_image_mse": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "nv_volume_mse": ([C.c_void_p, C.POINTER(Volume), C.c_void_p], C.c_int),
+    "nv_mse_f64": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "nv_ooc_create": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                       C.POINTER(C.c_void_p)], C.c_int),
+    "nv_ooc_destroy": ([C.c_void_p], C.c_int),
+    "nv_ooc_refresh": ([C.c_void_p, C.c_int, C.c_uint64, C.c_void_p], C.c_int),
+    "nv_ooc_sample": ([C.c_void_p, C.c_int64, C.c_uint64, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "nv_ooc_slots": ([C.c_void_p, C.POINTER(C.c_int)], C.c_int),
+    "nv_ooc_stats": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)], C.c_int),
     "nv_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
     "nv_profile_read": ([C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)], C.c_int),
     "nv_sync": ([C.c_void_p], C.c_int),
@@ -377,6 +385,68 @@ def image_mse(a, b, out=None):
     n = a.numel() // 4
     _check(lib().nv_image_mse(_dev(a, name="a"), _dev(b, name="b"), n, _dev(out, torch.float64, "out"), _stream()))
     return out
+
+
+def mse(a, b, out=None):
+    """FP64 mean squared error of two float32 CUDA tensors of the same size."""
+    if a.numel() != b.numel():
+        raise ValueError("mse: sizes differ")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=a.device)
+    _check(lib().nv_mse_f64(_dev(a.contiguous(), name="a"), _dev(b.contiguous(), name="b"), a.numel(),
+                            _dev(out, torch.float64, "out"), _stream()))
+    return out
+
+
+class BrickRing:
+    """Out-of-core sampling ring (nv_ooc): a device ring of bricks fed from
+    pinned host bricks (a CPU float32 tensor in pinned memory, kept alive here)."""
+
+    def __init__(self, host_bricks: torch.Tensor, shape, brick, ring_slots, seed=0):
+        if host_bricks.device.type != "cpu" or not host_bricks.is_pinned():
+            raise ValueError("host_bricks must be a pinned CPU tensor")
+        if host_bricks.dtype != torch.float32 or not host_bricks.is_contiguous():
+            raise ValueError("host_bricks must be contiguous float32")
+        self.host = host_bricks
+        nz, ny, nx = (int(v) for v in shape)
+        h = C.c_void_p()
+        _check(lib().nv_ooc_create(C.c_void_p(host_bricks.data_ptr()), nx, ny, nz, int(brick), int(ring_slots),
+                                   int(seed), C.byref(h)))
+        self._h = h
+        self.R = ring_slots
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nv_ooc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def refresh(self, count, seed):
+        _check(lib().nv_ooc_refresh(self._h, int(count), int(seed), _stream()))
+
+    def sample(self, n, seed, step, xyz=None, target=None):
+        if xyz is None:
+            xyz = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        if target is None:
+            target = torch.empty(n, dtype=torch.float32, device="cuda")
+        _check(lib().nv_ooc_sample(self._h, int(n), int(seed), int(step), _dev(xyz, name="xyz"),
+                                   _dev(target, name="target"), _stream()))
+        return xyz, target
+
+    def slots(self):
+        arr = (C.c_int * self.R)()
+        _check(lib().nv_ooc_slots(self._h, arr))
+        return list(arr)
+
+    def stats(self):
+        b, ms = C.c_int64(), C.c_double()
+        _check(lib().nv_ooc_stats(self._h, C.byref(b), C.byref(ms)))
+        return b.value, ms.value
 
 
 class NeuralVolumeFunction(torch.autograd.Function):

@@ -414,3 +414,32 @@ def test_volume_mse_zero_weights_closed_form():
     vol = I.blob_volume((5, 7, 6), seed=3)
     want = float(np.mean((0.5 - vol.astype(np.float64)) ** 2))
     assert O.volume_mse(net, params, vol) == pytest.approx(want, rel=1e-13)
+
+
+# ----------------------------------------------------------- out of core ----
+
+def test_brick_sample_stays_in_its_brick_and_interpolates():
+    vol = I.blob_volume(32, seed=9)
+    B = 8
+    slots = np.array([0, 5, 63, 17], np.int32)  # bricks of the 4x4x4 grid
+    xyz, t = O.brick_sample(vol, B, slots, seed=3, step=1, n=4000)
+    # every point lies within half a voxel of a voxel centre of one resident brick
+    v = xyz * 32 - 0.5
+    centre = np.rint(v)
+    assert np.all(np.abs(v - centre) <= 0.5 + 1e-5)
+    b = (centre[:, 2] // B) * 16 + (centre[:, 1] // B) * 4 + centre[:, 0] // B
+    assert set(np.unique(b).astype(int)) <= set(slots.tolist())
+    assert len(np.unique(b)) == 4
+    # the target is the volume's trilinear value there
+    np.testing.assert_array_equal(t, O.trilinear(vol, xyz))
+    # jitter spans the voxel: both halves are reached on every axis
+    off = v - centre
+    assert np.all(off.min(0) < -0.45) and np.all(off.max(0) > 0.45)
+
+
+def test_brick_sample_uniform_over_slots_and_voxels():
+    vol = I.blob_volume(16, seed=1)
+    slots = np.arange(8, dtype=np.int32)  # all 2x2x2 bricks of 8^3
+    xyz, _ = O.brick_sample(vol, 8, slots, seed=11, step=0, n=80000)
+    counts = np.histogramdd(xyz, bins=(2, 2, 2), range=[(0, 1)] * 3)[0].ravel()
+    assert np.all(np.abs(counts / 10000 - 1) < 0.05)
