@@ -208,40 +208,48 @@ def ncu_traffic(kernel):
     return None
 
 
-def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d):
+def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d, L, F):
     """Roofline of one kernel of the config-2 step from its live average launch time.
 
     Algorithmic bytes / FLOPs per launch (per unit x units):
       adam     34 B per parameter (read p, g, m, v; write p, m, v, g = 0, 16-bit shadow); 32 in FP32
-      scatter  dF read (4 D0 B per point) + the FP32 table gradient read and written once (8 B per entry)
-      encode   the 16-bit table shadow read once (2 B per entry) + 16-bit features written (2 D0 B per point)
-      mlp      tensor-core FLOPs per point: 2 (D0 64 + 64 64) forward + 2 (2 64 64 + 2 64 D0) backward;
-               FP32 path: the same products plus the output layer on CUDA cores"""
+      encode   per point: 8 corners x L levels x F 16-bit features read (8 L F 2 B) + the 16-bit
+               feature row written (2 D0 B) + the trilinear target (8 voxels read, 4 B written)
+      mlp      tensor-core path, per point: the feature row read (2 D0 B) + the target (4 B) + the
+               table-gradient scatter, 8 corners x L x F FP32 reductions (8 L F 4 B); also reported:
+               tensor FLOPs 2 (D0 64 + 64 64) forward + 2 (2 64 64 + 2 64 D0) backward.
+               FP32 path: those FLOPs on CUDA cores"""
     ms = avg[kind]
     D0 = d[0]
+    flops = 2 * batch * (D0 * 64 + 64 * 64) + 2 * batch * (2 * 64 * 64 + 2 * 64 * D0)
     if kind == "adam":
-        unit = n_params
         bytes_ = n_params * (32 + (2 if prec != "fp32" else 0))
         name = "k_adam"
-    elif kind == "scatter":
-        bytes_ = batch * D0 * 4 + n_table * 8
-        name = "k_scatter_tiles"
     elif kind == "encode":
-        bytes_ = n_table * 2 + batch * D0 * 2
+        bytes_ = batch * (8 * L * F * 2 + 2 * D0 + 8 * 4 + 4)
         name = "k_encode_tiles"
+    elif prec != "fp32":
+        bytes_ = batch * (2 * D0 + 4 + 8 * L * F * 4)
+        name = "k_mlp_tc"
     else:
         bytes_ = None
-        name = "k_mlp_tc" if prec != "fp32" else "k_mlp_f32"
+        name = "k_mlp_f32"
     if bytes_ is not None:
         ach = bytes_ / (ms / 1e3) / 1e9
         r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
              "frac": ach / pk["hbm_gbs"], "traffic": ncu_traffic(name), "peak_kind": pk_kind + " (copy)",
              "algorithmic_bytes_per_launch": bytes_, "avg_ms": ms}
-        if kind in ("scatter", "encode"):
-            r["limiter"] = ("L2: scattered 32-byte sector requests (gathers) / vector reductions (scatter), "
-                            "not DRAM bytes; see profiles/tc_train_kernels_cfg2.md")
+        if kind == "encode":
+            r["limiter"] = ("L1-to-L2 request rate of the scattered 32-byte sector gathers; coarse levels hit "
+                            "in L1 and the 16-bit tables in L2, so DRAM carries a fraction of these bytes")
+        elif kind == "mlp":
+            peak_t = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+            ach_t = flops / (ms / 1e3) / 1e12
+            r["limiter"] = ("L2 vector reductions of the fused table-gradient scatter, which resolve in L2 "
+                            "(the 64 MiB FP32 table gradient stays resident); the tensor pipe is not the limit")
+            r["tensor"] = {"achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s", "frac": ach_t / peak_t,
+                           "algorithmic_flops_per_launch": flops}
         return r
-    flops = 2 * batch * (D0 * 64 + 64 * 64) + 2 * batch * (2 * 64 * 64 + 2 * 64 * D0)
     ach = flops / (ms / 1e3) / 1e12
     if prec == "fp32":
         peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -295,7 +303,7 @@ def run_ours(args):
     clocks = Clocks(local)
     clocks.start()
     net.profile(True)
-    for k in ("mlp", "adam", "finish", "encode", "scatter"):
+    for k in ("mlp", "adam", "finish", "encode"):
         net.profile_read(k)
     barrier(ws)
     torch.cuda.synchronize()
@@ -346,14 +354,14 @@ def run_ours(args):
     if rank != 0:
         return 0
     pk, pk_kind = peaks()
-    kt = {k: net.profile_read(k) for k in ("encode", "scatter")}
+    kt = {k: net.profile_read(k) for k in ("encode",)}
     kt["mlp"], kt["adam"], kt["finish"] = k_mlp, k_adam, k_fin
     avg = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in kt.items()}
     n_params, n_table = net.n_params, net.n_table
     d = c.dims
     D0 = d[0]
-    roof = roofline_of(max(("encode", "mlp", "scatter", "adam"), key=lambda k: kt[k][0]), avg, prec, pk, pk_kind,
-                       batch, n_params, n_table, d)
+    roof = roofline_of(max(("encode", "mlp", "adam"), key=lambda k: kt[k][0]), avg, prec, pk, pk_kind,
+                       batch, n_params, n_table, d, c.L, c.F)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -366,7 +374,7 @@ def run_ours(args):
         "roofline": roof,
         "kernels_ms_per_step": {k: v for k, v in avg.items() if v > 0},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": batch * 16, "d2h_bytes_per_step": 8},
-        "gpu_launches": args.steps * sum(1 for k in ("encode", "mlp", "scatter", "adam", "finish") if kt[k][1]),
+        "gpu_launches": args.steps * sum(1 for k in ("encode", "mlp", "adam", "finish") if kt[k][1]),
         "clocks": clk,
     }
     if ws == 1 and args.extras:

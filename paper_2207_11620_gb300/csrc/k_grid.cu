@@ -1,10 +1,11 @@
-// k_grid.cu -- the memory-bound halves of the tensor-core path: the hash-grid
-// gather that produces FP16/BF16 features in the tensor-core tile layout
-// (A-1..A-3), and the scatter of the input gradient into the FP32 table
-// gradient (A-7).  Both are kept out of the tensor-core kernel so that they
-// run at full occupancy: each thread issues all the loads (or atomics) of its
-// levels back to back and dozens of warps per SM keep the L1-to-L2 request
-// path busy.
+// k_grid.cu -- the gather half of the tensor-core path: the hash-grid lookup
+// that produces FP16/BF16 features in the tensor-core tile layout (A-1..A-3),
+// and, for points the training step samples itself, their trilinear ground
+// truth (A-9).  It runs ahead of the MLP kernel at full occupancy: each thread
+// issues all the loads of its levels back to back and dozens of warps per SM
+// keep the L1-to-L2 request path busy, which the tensor-core kernel, with its
+// few large CTAs, could not.  The adjoint scatter (A-7) runs inside the MLP
+// kernel's backward epilogue (k_tc.cu).
 //
 // Work item = (point, chunk of 8 features): with F features per level a chunk
 // covers 8 / F levels.  Items are chunk-major, so neighbouring threads handle
@@ -17,7 +18,8 @@ namespace {
 
 template <int F, bool BF>
 __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t *__restrict__ shadow, PointSrc ps,
-                                                      ChunkSpan cs, uint8_t *__restrict__ feat) {
+                                                      ChunkSpan cs, uint8_t *__restrict__ feat,
+                                                      float *__restrict__ tgt) {
   const int D0 = nd.dims[0];
   const int C = D0 / 8;
   const int64_t n = chunk_count(cs);
@@ -32,6 +34,7 @@ __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t
     return;
   }
   const float3 x = point_at(ps, cs.off + q);
+  if (tgt && c == 0) tgt[q] = nv_trilinear(ps.vol.data_dev, ps.vol.nx, ps.vol.ny, ps.vol.nz, x.x, x.y, x.z);
   float f8[8];
   gather_levels<F, BF, 8 / F>(shadow, nd, c * (8 / F), x.x, x.y, x.z, f8);
   uint4 u;
@@ -42,33 +45,13 @@ __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t
   *reinterpret_cast<uint4 *>(dst) = u;
 }
 
-// dF rows are FP32 [cap][D0], already divided by the loss scale.
-template <int F>
-__global__ void __launch_bounds__(256) k_scatter_tiles(NetDesc nd, PointSrc ps, ChunkSpan cs,
-                                                       const float *__restrict__ dF, float *grads) {
-  const int D0 = nd.dims[0];
-  const int C = D0 / 8;
-  const int64_t n = chunk_count(cs);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * C) return;
-  const int c = (int)(i / n);
-  const int64_t q = i - (int64_t)c * n;
-  const float3 x = point_at(ps, cs.off + q);
-  const float4 *src = reinterpret_cast<const float4 *>(dF + q * D0 + c * 8);
-  const float4 a = __ldg(src), b = __ldg(src + 1);
-  const float g8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-  for (int k = 0; k < 8 / F; ++k) {
-    const int l = c * (8 / F) + k;
-    scatter_level<F>(grads + (size_t)l * nd.T * F, nd.T - 1, (float)nd.res[l], x.x, x.y, x.z, g8 + k * F);
-  }
-}
-
 inline unsigned grid_for(int64_t items) { return (unsigned)((items + 255) / 256); }
 
 }  // namespace
 
-nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat) {
+// tgt (nullable): [cap] targets of a Philox training sample (ps.kind == 2).
+nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat,
+                              float *tgt) {
   const int C = c->nd.dims[0] / 8;
   const int64_t npad = (cs.cap + 127) & ~int64_t(127);
   if (npad == 0) return NV_OK;
@@ -77,28 +60,15 @@ nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSp
   const bool bf = c->prec == NV_BF16;
   switch (c->nd.F) {
     case 2:
-      if (bf) k_encode_tiles<2, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat);
-      else k_encode_tiles<2, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat);
+      if (bf) k_encode_tiles<2, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt);
+      else k_encode_tiles<2, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt);
       break;
     case 4:
-      if (bf) k_encode_tiles<4, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat);
-      else k_encode_tiles<4, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat);
+      if (bf) k_encode_tiles<4, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt);
+      else k_encode_tiles<4, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt);
       break;
     default:
       return nv_fail(NV_ERR_UNSUPPORTED, "tensor-core encode: F=%d", c->nd.F);
   }
   return nv_cuda_check(cudaGetLastError(), "k_encode_tiles launch");
-}
-
-nv_status launch_scatter_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, const float *dF,
-                               float *grads) {
-  const int C = c->nd.dims[0] / 8;
-  if (cs.cap == 0) return NV_OK;
-  const unsigned g = grid_for(cs.cap * C);
-  switch (c->nd.F) {
-    case 2: k_scatter_tiles<2><<<g, 256, 0, c->stream>>>(c->nd, ps, cs, dF, grads); break;
-    case 4: k_scatter_tiles<4><<<g, 256, 0, c->stream>>>(c->nd, ps, cs, dF, grads); break;
-    default: return nv_fail(NV_ERR_UNSUPPORTED, "tensor-core scatter: F=%d", c->nd.F);
-  }
-  return nv_cuda_check(cudaGetLastError(), "k_scatter_tiles launch");
 }

@@ -3,17 +3,20 @@
 // {16, 32, 64} inputs and two hidden layers of 64 (Sec. 3.1's fully fused MLP,
 // re-designed for sm_103a), and the launch sequence of the tensor-core path:
 //
-//   k_encode_tiles   gather + trilinear blend -> features in tile layout (k_grid.cu)
+//   k_encode_tiles   gather + trilinear blend -> features in tile layout, and
+//                    the targets of a sampled training batch (k_grid.cu)
 //   k_mlp_tc         per 128-point tile: features arrive by one bulk async copy
 //                    (double-buffered, the next tile's copy overlaps this one),
 //                    layer 0 / 1 products, ReLU and the FP32 output layer; in
 //                    training the backward products, the weight gradients
 //                    accumulated in tensor memory over all tiles of the CTA,
-//                    and the per-point input gradient dF written out
-//   k_scatter_tiles  dF into the FP32 table gradient (k_grid.cu)
+//                    and the per-point input gradient dF, which each thread
+//                    scatters straight into the FP32 table gradient (A-7)
 //
-// The three run on chunks of at most kChunk points so the features and dF of
-// a chunk (16 MB + 32 MB at D0 = 32) stay in L2 between the kernels.
+// The two run on chunks of at most kChunk points so the features of a chunk
+// (16 MB at D0 = 32) stay in L2 between the kernels.  The scatter's vector
+// reductions keep the load/store path busy while the CTA's other phases wait
+// on the tensor core, so the MLP and the scatter overlap inside one kernel.
 //
 // One CTA = 256 threads; a tile is 128 points.  Point r of the tile is TMEM
 // lane r and is shared by threads r and r + 128: each handles half of the 64
@@ -30,9 +33,8 @@
 #include "tc_grid.cuh"
 #include "tc_ptx.cuh"
 
-nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat);
-nv_status launch_scatter_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, const float *dF,
-                               float *grads);
+nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat,
+                              float *tgt);
 
 namespace {
 
@@ -105,6 +107,24 @@ __device__ __forceinline__ void st_row8(uint8_t *base, int r, int c, int K, cons
   *reinterpret_cast<uint4 *>(base + tile_off(r, c * 8, K)) = u;
 }
 
+// Add n scaled values to 16-byte aligned dst with n / 4 vector reductions,
+// skipping all-zero groups; returns whether any value is not finite (that
+// group is then left out).
+template <int n>
+__device__ __forceinline__ bool red_row(float *dst, const float *v, float s) {
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < n; j += 4) {
+    const float4 g = make_float4(v[j] * s, v[j + 1] * s, v[j + 2] * s, v[j + 3] * s);
+    if (!isfinite(g.x) || !isfinite(g.y) || !isfinite(g.z) || !isfinite(g.w)) {
+      bad = true;
+      continue;
+    }
+    if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) atomicAdd(reinterpret_cast<float4 *>(dst + j), g);
+  }
+  return bad;
+}
+
 __device__ __forceinline__ uint64_t desc_k(uint32_t saddr, int K) {  // K-major [rows][K]
   return tc::smem_desc(saddr, 128, (uint32_t)K * 16);
 }
@@ -115,13 +135,14 @@ __device__ __forceinline__ uint64_t desc_mn(uint32_t saddr, int Kphys) {  // MN-
 
 // MODE_INFER: y = sigmoid(MLP(f)).  MODE 3: accumulate (y - vol)^2 into acc.
 // MODE_TRAIN: loss += (y - t)^2, dF = d(loss / n)/df.  MODE_BACKWARD: dF = dL/dy * dy/df.
-// Weight gradients of TRAIN / BACKWARD are added into a.grads.
+// TRAIN / BACKWARD add the weight gradients and the table gradient w_corner * dF
+// into a.grads.  tgt_buf: the targets of a sampled training batch, [chunk rows].
 template <int D0, bool BF, int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_mlp_tc(NetDesc nd, const float *__restrict__ params,
                                                         const uint16_t *__restrict__ shadow, MlpArgs a,
                                                         PointSrc ps, ChunkSpan cs,
-                                                        const uint8_t *__restrict__ feat, float *__restrict__ dF,
-                                                        double *acc) {
+                                                        const uint8_t *__restrict__ feat,
+                                                        const float *__restrict__ tgt_buf, double *acc) {
   using P = Plan<D0, MODE>;
   constexpr bool kBwd = P::kBwd;
   constexpr int HH = kH / 2;  // hidden columns per thread
@@ -232,12 +253,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mlp_tc(NetDesc nd, const float 
       if (MODE == 3) {
         tgt = a.vol.data_dev[p];
       } else if (MODE == MODE_TRAIN) {
-        if (a.in) {
-          tgt = a.in[p];
-        } else {
-          const float3 x = point_at(ps, p);
-          tgt = nv_trilinear(a.vol.data_dev, a.vol.nx, a.vol.ny, a.vol.nz, x.x, x.y, x.z);
-        }
+        tgt = a.in ? a.in[p] : tgt_buf[q];
       } else if (MODE == MODE_BACKWARD) {
         tgt = a.in[p];
       }
@@ -399,20 +415,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_mlp_tc(NetDesc nd, const float 
       }
       if (wait_mma()) { failed = true; break; }
       first = false;
-      // ---- this thread's half of dF, unscaled, to the chunk's dF rows ----
+      // ---- this thread's half of dF, unscaled, scattered into the table gradient ----
       float df[DH];
 #pragma unroll
       for (int c = 0; c < DH / 8; ++c) tc::tmem_ld8(tD2 + lane_base + hh * DH + c * 8, df + c * 8);
       tc::tmem_ld_wait();
       tc::fence_before_sync();
       if (valid) {
-        float4 *dst = reinterpret_cast<float4 *>(dF + q * D0 + hh * DH);
 #pragma unroll
-        for (int i = 0; i < DH; i += 4) {
-          float4 v = make_float4(df[i] * inv_scale, df[i + 1] * inv_scale, df[i + 2] * inv_scale,
-                                 df[i + 3] * inv_scale);
-          if (!isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w)) bad = true;
-          dst[i / 4] = v;
+        for (int i = 0; i < DH; ++i) {
+          df[i] *= inv_scale;
+          if (!isfinite(df[i])) bad = true;
+        }
+        const float3 x = point_at(ps, p);
+        if (nd.F == 2) {
+#pragma unroll
+          for (int k = 0; k < DH / 2; ++k) {
+            const int l = hh * (DH / 2) + k;
+            scatter_level<2>(a.grads + (size_t)l * nd.T * 2, nd.T - 1, (float)nd.res[l], x.x, x.y, x.z,
+                             df + 2 * k);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < DH / 4; ++k) {
+            const int l = hh * (DH / 4) + k;
+            scatter_level<4>(a.grads + (size_t)l * nd.T * 4, nd.T - 1, (float)nd.res[l], x.x, x.y, x.z,
+                             df + 4 * k);
+          }
         }
       }
     }
@@ -439,33 +468,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_mlp_tc(NetDesc nd, const float 
         } else {
           if (warp < 2) row = warp * 32 + lane;
         }
+        // 16-byte vector reductions: all CTAs add into the same few thousand
+        // addresses, so fewer, wider reductions shorten the kernel's tail
+        // (the weight offsets are multiples of 4 floats, checked on the host)
 #pragma unroll
         for (int c = 0; c < kH / 16; ++c) {
           float v[16];
           tc::tmem_ld16(tmem + P::kColG1 + lane_base + c * 16, v);
           tc::tmem_ld_wait();
-          if (row >= 0) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const float gv = v[i] * inv_scale;
-              if (!isfinite(gv)) bad = true;
-              else if (gv != 0.f) atomicAdd(gw + nd.w_off[1] + row * kH + c * 16 + i, gv);
-            }
-          }
+          if (row >= 0) bad |= red_row<16>(gw + nd.w_off[1] + row * kH + c * 16, v, inv_scale);
         }
 #pragma unroll
         for (int c = 0; c < D0 / 8; ++c) {
           float v[8];
           tc::tmem_ld8(tmem + P::kColG0 + lane_base + c * 8, v);
           tc::tmem_ld_wait();
-          if (row >= 0) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const float gv = v[i] * inv_scale;
-              if (!isfinite(gv)) bad = true;
-              else if (gv != 0.f) atomicAdd(gw + nd.w_off[0] + row * D0 + c * 8 + i, gv);
-            }
-          }
+          if (row >= 0) bad |= red_row<8>(gw + nd.w_off[0] + row * D0 + c * 8, v, inv_scale);
         }
       }
     }
@@ -488,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mlp_tc(NetDesc nd, const float 
 
 template <int D0, bool BF, int MODE>
 nv_status launch_mlp(const nv_ctx *c, const MlpArgs &a, const PointSrc &ps, const ChunkSpan &cs,
-                     const uint8_t *feat, float *dF, double *acc) {
+                     const uint8_t *feat, const float *tgt, double *acc) {
   using P = Plan<D0, MODE>;
   // tensor memory holds 512 columns per SM: size the shared-memory request so
   // that no more CTAs fit on an SM than their columns allow
@@ -524,29 +542,29 @@ nv_status launch_mlp(const nv_ctx *c, const MlpArgs &a, const PointSrc &ps, cons
   if (grid < 1) return NV_OK;
   kern<<<(unsigned)grid, kThreads, bytes, c->stream>>>(c->nd, c->params,
                                                         reinterpret_cast<const uint16_t *>(c->shadow), a, ps, cs,
-                                                        feat, dF, acc);
+                                                        feat, tgt, acc);
   return nv_cuda_check(cudaGetLastError(), "k_mlp_tc launch");
 }
 
 template <int D0, bool BF>
 nv_status dispatch_mode(const nv_ctx *c, int mode, const MlpArgs &a, const PointSrc &ps, const ChunkSpan &cs,
-                        const uint8_t *feat, float *dF, double *acc) {
+                        const uint8_t *feat, const float *tgt, double *acc) {
   switch (mode) {
-    case MODE_INFER: return launch_mlp<D0, BF, MODE_INFER>(c, a, ps, cs, feat, dF, acc);
-    case MODE_BACKWARD: return launch_mlp<D0, BF, MODE_BACKWARD>(c, a, ps, cs, feat, dF, acc);
-    case MODE_TRAIN: return launch_mlp<D0, BF, MODE_TRAIN>(c, a, ps, cs, feat, dF, acc);
-    case 3: return launch_mlp<D0, BF, 3>(c, a, ps, cs, feat, dF, acc);
+    case MODE_INFER: return launch_mlp<D0, BF, MODE_INFER>(c, a, ps, cs, feat, tgt, acc);
+    case MODE_BACKWARD: return launch_mlp<D0, BF, MODE_BACKWARD>(c, a, ps, cs, feat, tgt, acc);
+    case MODE_TRAIN: return launch_mlp<D0, BF, MODE_TRAIN>(c, a, ps, cs, feat, tgt, acc);
+    case 3: return launch_mlp<D0, BF, 3>(c, a, ps, cs, feat, tgt, acc);
   }
   return nv_fail(NV_ERR_ARG, "bad MLP mode %d", mode);
 }
 
 template <bool BF>
 nv_status dispatch_shape(const nv_ctx *c, int mode, const MlpArgs &a, const PointSrc &ps, const ChunkSpan &cs,
-                         const uint8_t *feat, float *dF, double *acc) {
+                         const uint8_t *feat, const float *tgt, double *acc) {
   switch (c->nd.dims[0]) {
-    case 16: return dispatch_mode<16, BF>(c, mode, a, ps, cs, feat, dF, acc);
-    case 32: return dispatch_mode<32, BF>(c, mode, a, ps, cs, feat, dF, acc);
-    case 64: return dispatch_mode<64, BF>(c, mode, a, ps, cs, feat, dF, acc);
+    case 16: return dispatch_mode<16, BF>(c, mode, a, ps, cs, feat, tgt, acc);
+    case 32: return dispatch_mode<32, BF>(c, mode, a, ps, cs, feat, tgt, acc);
+    case 64: return dispatch_mode<64, BF>(c, mode, a, ps, cs, feat, tgt, acc);
   }
   return nv_fail(NV_ERR_UNSUPPORTED, "tensor-core MLP: no kernel for L*F=%d", c->nd.dims[0]);
 }
@@ -556,22 +574,24 @@ nv_status dispatch_shape(const nv_ctx *c, int mode, const MlpArgs &a, const Poin
 bool tc_supported(const NetDesc &nd) {
   if (nd.n_dims != 4 || nd.dims[1] != kH || nd.dims[2] != kH || nd.dims[3] != 1) return false;
   const int F = nd.F, D0 = nd.dims[0];
+  // the weight-gradient reductions are 16-byte vectors
+  if (nd.n_table % 4 || nd.w_off[0] % 4 || nd.w_off[1] % 4) return false;
   return (F == 2 && (D0 == 16 || D0 == 32 || D0 == 64)) || (F == 4 && (D0 == 32 || D0 == 64));
 }
 
 // Scratch of the tensor-core path: one chunk of features (16-bit, tile layout)
-// and of dF (FP32 rows), allocated on first use.
+// and of sampled training targets (FP32), allocated on first use.
 static nv_status tc_scratch(nv_ctx *c, int64_t points) {
   const int64_t cap = points < kChunk ? ((points + kTP - 1) / kTP) * kTP : kChunk;
   if (c->tc_cap >= cap) return NV_OK;
   cudaFree(c->tc_feat);
-  cudaFree(c->tc_df);
+  cudaFree(c->tc_tgt);
   c->tc_feat = nullptr;
-  c->tc_df = nullptr;
+  c->tc_tgt = nullptr;
   c->tc_cap = 0;
   const int D0 = c->nd.dims[0];
   cudaError_t e = cudaMalloc(&c->tc_feat, (size_t)cap * D0 * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&c->tc_df, (size_t)cap * D0 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->tc_tgt, (size_t)cap * 4);
   if (e != cudaSuccess) return nv_cuda_check(e, "tensor-core scratch");
   c->tc_cap = cap;
   return NV_OK;
@@ -597,24 +617,18 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
     ps.seed = a.seed;
     ps.step = a.sample_step;
   }
-  const bool bwd = mode == MODE_TRAIN || mode == MODE_BACKWARD;
+  float *tgt = (mode == MODE_TRAIN && ps.kind == 2) ? c->tc_tgt : nullptr;
   for (int64_t off = 0; off < n_upper; off += c->tc_cap) {
     ChunkSpan cs{n_dev, n_mult, a.n, off, n_upper - off < c->tc_cap ? n_upper - off : c->tc_cap};
     int tk = prof_begin(c);
-    s = launch_encode_tiles(c, ps, cs, c->tc_feat);
+    s = launch_encode_tiles(c, ps, cs, c->tc_feat, tgt);
     prof_end(c, NV_K_ENCODE, tk);
     if (s != NV_OK) return s;
     tk = prof_begin(c);
-    s = c->prec == NV_BF16 ? dispatch_shape<true>(c, mode, a, ps, cs, c->tc_feat, c->tc_df, acc)
-                           : dispatch_shape<false>(c, mode, a, ps, cs, c->tc_feat, c->tc_df, acc);
+    s = c->prec == NV_BF16 ? dispatch_shape<true>(c, mode, a, ps, cs, c->tc_feat, tgt, acc)
+                           : dispatch_shape<false>(c, mode, a, ps, cs, c->tc_feat, tgt, acc);
     prof_end(c, NV_K_MLP, tk);
     if (s != NV_OK) return s;
-    if (bwd) {
-      tk = prof_begin(c);
-      s = launch_scatter_tiles(c, ps, cs, c->tc_df, a.grads);
-      prof_end(c, NV_K_SCATTER, tk);
-      if (s != NV_OK) return s;
-    }
   }
   return NV_OK;
 }

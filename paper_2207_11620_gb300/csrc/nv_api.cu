@@ -86,7 +86,7 @@ static void ctx_free(nv_ctx *c) {
   cudaFree(c->ds);
   cudaFree(c->batch);
   cudaFree(c->tc_feat);
-  cudaFree(c->tc_df);
+  cudaFree(c->tc_tgt);
   delete c;
 }
 
@@ -366,7 +366,7 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
     NV_TRY(launch_mlp_f32(c, MODE_TRAIN, a));
     prof_end(c, NV_K_MLP, tk0);
   } else {
-    NV_TRY(launch_mlp_tc(c, MODE_TRAIN, a));  // times its encode / MLP / scatter kernels itself
+    NV_TRY(launch_mlp_tc(c, MODE_TRAIN, a));  // times its encode and MLP kernels itself
   }
   int tk = prof_begin(c);
   NV_TRY(launch_adam(c));

@@ -54,7 +54,7 @@ struct nv_ctx {
   int num_sms;
   struct Prof *prof;                        // kernel timing (nv_profile_enable), NULL when off
   uint8_t *tc_feat;                         // tensor-core path: one chunk of 16-bit features (tile layout)
-  float *tc_df;                             // tensor-core path: one chunk of input gradients
+  float *tc_tgt;                            // tensor-core path: one chunk of sampled training targets
   int64_t tc_cap;                           // points per chunk of the two above
 };
 
