@@ -227,6 +227,23 @@ double or_loss_l2(const double *y, const float *t, int64_t n) {
   return n > 0 ? s / (double)n : 0.0;
 }
 
+/* L1 loss, the paper's default (Sec. 3.1, App. B): the mean over the batch of
+ * |y - t|.  Its derivative in y is sign(y - t) / n, taken as 0 where y == t. */
+double or_loss_l1(const double *y, const float *t, int64_t n) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += fabs(y[i] - (double)t[i]);
+  return n > 0 ? s / (double)n : 0.0;
+}
+
+/* Exponentially decaying learning rate (App. B: decay start, interval and base
+ * around Adam).  Reading: the rate of the optimizer step with 0-based index k
+ * is lr0 * base^d with d = 0 while k < start and d = floor((k - start) /
+ * interval) + 1 from then on, so the first decay applies to step `start`. */
+double or_lr_at(double lr0, int k, int start, int interval, double base) {
+  if (k < start || interval <= 0) return lr0;
+  return lr0 * pow(base, (double)((k - start) / interval + 1));
+}
+
 /* A-6 / A-7: analytic backward of encode + MLP for upstream gradients dL/dy.
  * Accumulates (+=) into grads, laid out like params (tables then weights).
  * Chain rule: dz_out = dL/dy * y (1 - y); dW_k += delta_k a_k^T;
@@ -300,21 +317,28 @@ void or_adam(double *p, const double *g, double *m, double *v, int64_t n, int t,
   }
 }
 
-/* One training step (Sec. 4): forward on the batch, L2 loss, backward with
- * dL/dy = 2 (y - t) / n, Adam.  grads is scratch of the params' size and is
- * left holding this step's gradient.  Returns the loss before the update. */
+/* One training step (Sec. 4): forward on the batch, loss (l1 == 0: L2 with
+ * dL/dy = 2 (y - t) / n; l1 != 0: L1 with dL/dy = sign(y - t) / n), backward,
+ * Adam at step t (counted from 1) with the learning rate or_lr_at(lr, t - 1,
+ * ...).  grads is scratch of the params' size and is left holding this step's
+ * gradient.  Returns the loss before the update. */
 double or_train_step(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
                      double *params, double *grads, double *m, double *v, int64_t n_params,
                      const float *xyz, const float *target, int64_t n, int t,
-                     double lr, double b1, double b2, double eps, double l2) {
+                     double lr, double b1, double b2, double eps, double l2,
+                     int l1, int decay_start, int decay_interval, double decay_base) {
   double *y = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
   double *dy = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
   or_forward(L, F, log2T, res, dims, n_dims, params, xyz, n, y);
-  double loss = or_loss_l2(y, target, n);
-  for (int64_t i = 0; i < n; ++i) dy[i] = 2.0 * (y[i] - (double)target[i]) / (double)n;
+  double loss = l1 ? or_loss_l1(y, target, n) : or_loss_l2(y, target, n);
+  for (int64_t i = 0; i < n; ++i) {
+    double d = y[i] - (double)target[i];
+    dy[i] = l1 ? (double)((d > 0.0) - (d < 0.0)) / (double)n : 2.0 * d / (double)n;
+  }
   memset(grads, 0, sizeof(double) * n_params);
   or_backward(L, F, log2T, res, dims, n_dims, params, xyz, n, dy, grads);
-  or_adam(params, grads, m, v, n_params, t, lr, b1, b2, eps, l2);
+  or_adam(params, grads, m, v, n_params, t, or_lr_at(lr, t - 1, decay_start, decay_interval, decay_base),
+          b1, b2, eps, l2);
   free(y); free(dy);
   return loss;
 }

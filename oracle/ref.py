@@ -71,13 +71,18 @@ def lib():
                                  C.c_int64, _f64p]
         L.or_loss_l2.argtypes = [_f64p, _f32p, C.c_int64]
         L.or_loss_l2.restype = C.c_double
+        L.or_loss_l1.argtypes = [_f64p, _f32p, C.c_int64]
+        L.or_loss_l1.restype = C.c_double
+        L.or_lr_at.argtypes = [C.c_double, C.c_int, C.c_int, C.c_int, C.c_double]
+        L.or_lr_at.restype = C.c_double
         L.or_backward.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
                                   C.c_int64, _f64p, _f64p]
         L.or_adam.argtypes = [_f64p, _f64p, _f64p, _f64p, C.c_int64, C.c_int, C.c_double,
                               C.c_double, C.c_double, C.c_double, C.c_double]
         L.or_train_step.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f64p,
                                     _f64p, _f64p, C.c_int64, _f32p, _f32p, C.c_int64, C.c_int,
-                                    C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
+                                    C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.c_int, C.c_int, C.c_int, C.c_double]
         L.or_train_step.restype = C.c_double
         L.or_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.or_sample_points.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int64, _f32p]
@@ -204,6 +209,15 @@ def loss_l2(y, t):
     return float(lib().or_loss_l2(_f64(y), _f32(t), len(y)))
 
 
+def loss_l1(y, t):
+    return float(lib().or_loss_l1(_f64(y), _f32(t), len(y)))
+
+
+def lr_at(lr0, k, start, interval, base):
+    """Learning rate of the 0-based optimizer step k under the exponential decay."""
+    return float(lib().or_lr_at(lr0, int(k), int(start), int(interval), base))
+
+
 def backward(net: Net, params, xyz, dL_dy):
     xyz = _f32(xyz)
     g = np.zeros(net.n_params, dtype=np.float64)
@@ -220,14 +234,17 @@ def adam(p, g, m, v, t, lr=1e-2, b1=0.9, b2=0.999, eps=1e-15, l2=0.0):
 class Trainer:
     """Oracle training state: FP64 params, Adam moments and the step count."""
 
-    def __init__(self, net: Net, params, lr=1e-2, b1=0.9, b2=0.999, eps=1e-15, l2=0.0):
+    def __init__(self, net: Net, params, lr=1e-2, b1=0.9, b2=0.999, eps=1e-15, l2=0.0, loss="l2",
+                 decay_start=2000, decay_interval=1000, decay_base=0.99):
         self.net = net
         self.params = _f64(params).copy()
         self.grads = np.zeros_like(self.params)
         self.m = np.zeros_like(self.params)
         self.v = np.zeros_like(self.params)
         self.t = 0
-        self.hp = (lr, b1, b2, eps, l2)
+        if loss not in ("l1", "l2"):
+            raise ValueError(loss)
+        self.hp = (lr, b1, b2, eps, l2, int(loss == "l1"), int(decay_start), int(decay_interval), decay_base)
 
     def step(self, xyz, target):
         net = self.net

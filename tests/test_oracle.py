@@ -254,6 +254,64 @@ def test_train_step_reduces_loss():
     assert losses[-1] < 0.5 * losses[0]
 
 
+@pytest.mark.parametrize("start,interval,base", [(2000, 1000, 0.99), (3, 2, 0.5), (0, 1, 0.9), (5, 7, 0.75)])
+def test_lr_decay_matches_procedural_schedule(start, interval, base):
+    # App. B's schedule run as a procedure: the rate starts at lr0 and is
+    # multiplied by `base` when step `start` begins and then every `interval` steps
+    lr0, lr = 5e-3, 5e-3
+    for k in range(start + 5 * interval + 3):
+        if k >= start and (k - start) % interval == 0:
+            lr *= base
+        assert O.lr_at(lr0, k, start, interval, base) == pytest.approx(lr, rel=1e-13), k
+
+
+def test_l1_loss_known_values():
+    y = np.array([0.5, 0.25, 0.75, 0.125])
+    t = np.array([0.25, 0.5, 0.75, 0.0], np.float32)
+    assert O.loss_l1(y, t) == pytest.approx((0.25 + 0.25 + 0.0 + 0.125) / 4, rel=1e-15)
+    assert O.loss_l2(y, t) == pytest.approx((0.0625 + 0.0625 + 0.0 + 0.015625) / 4, rel=1e-15)
+
+
+@pytest.mark.parametrize("loss", ["l1", "l2"])
+def test_train_step_gradient_matches_finite_differences(loss):
+    # with lr = 0 the step leaves the parameters alone and its gradient scratch
+    # holds d(loss)/d(params); compare with central differences of the loss
+    net, params, x, _ = _fd_setup()
+    y0 = O.forward(net, params, x)
+    rng = np.random.default_rng(11)
+    t = (y0 + rng.choice([-0.05, 0.05], size=y0.shape)).astype(np.float32)  # away from the L1 kink
+    tr = O.Trainer(net, params, lr=0.0, loss=loss)
+    l0 = tr.step(x, t)
+    lossf = O.loss_l1 if loss == "l1" else O.loss_l2
+    assert l0 == pytest.approx(lossf(y0, t), rel=1e-14)
+    np.testing.assert_array_equal(tr.params, params.astype(np.float64))
+    g = tr.grads
+    touched = np.flatnonzero(g[: net.n_table])
+    pick = np.concatenate([rng.choice(touched, 30, replace=False),
+                           net.n_table + rng.choice(net.n_weights, 30, replace=False)])
+    eps = 1e-6
+    for i in pick:
+        p1, p2 = params.astype(np.float64), params.astype(np.float64)
+        p1[i] += eps
+        p2[i] -= eps
+        fd = (lossf(O.forward(net, p1, x), t) - lossf(O.forward(net, p2, x), t)) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])) + 1e-10, (i, fd, g[i])
+
+
+@pytest.mark.parametrize("start,expect_decays", [(0, 1), (1, 0)])
+def test_train_step_first_update_uses_decayed_rate(start, expect_decays):
+    # Adam's first update moves every parameter with a non-zero gradient by
+    # exactly its learning rate; with decay_start = 0 that rate is already lr0 * base
+    net, params, x, _ = _fd_setup()
+    t = np.full(x.shape[0], 0.9, np.float32)
+    tr = O.Trainer(net, params, lr=1e-3, loss="l2", decay_start=start, decay_interval=4, decay_base=0.5)
+    tr.step(x, t)
+    moved = np.abs(tr.grads) > 1e-6  # eps = 1e-15 then changes the step by < 1e-9 relative
+    assert moved.sum() > 500
+    step = np.abs(tr.params - params.astype(np.float64))[moved]
+    np.testing.assert_allclose(step, 1e-3 * 0.5 ** expect_decays, rtol=1e-9)
+
+
 # -------------------------------------------------------------- sampling ----
 
 def test_philox_known_answers(golden_dir):
