@@ -91,9 +91,20 @@ typedef struct {
   int nx, ny, nz;          /* volume dimensions the grid was built for */
 } nv_macrocells;
 
+/* Adam (Kingma & Ba; Sec. 3.1, App. B) with an exponentially decaying rate:
+ * the optimizer step with 0-based index k (steps skipped after an FP16
+ * overflow are not counted) uses lr * decay_base^d, d = 0 while k <
+ * decay_start and d = floor((k - decay_start) / decay_interval) + 1 from then
+ * on.  l2_reg * p is added to the gradient before the moments.  decay_base = 1
+ * (or decay_interval <= 0) keeps the rate constant. */
 typedef struct {
   float lr, beta1, beta2, eps, l2_reg;
+  int decay_start, decay_interval;
+  float decay_base;
 } nv_adam_cfg;
+
+/* Training loss (Sec. 3.1: L1 by default in the paper; L2 where Sec. 7 names it). */
+typedef enum { NV_LOSS_L2 = 0, NV_LOSS_L1 = 1 } nv_loss;
 
 /* ---- context ------------------------------------------------------------ */
 
@@ -102,7 +113,8 @@ typedef struct {
  * host), MLP widths mlp_dims[0..n_dims-1] with mlp_dims[0] == L*F and
  * mlp_dims[n_dims-1] == 1 (ReLU hidden layers, sigmoid output, no biases).
  * prec selects the MLP arithmetic (nv_prec).  Parameters start at zero; Adam
- * defaults are lr 1e-2, beta (0.9, 0.999), eps 1e-15, l2 0.  Tensor-core
+ * defaults are lr 1e-2, beta (0.9, 0.999), eps 1e-15, l2 0, with the paper's
+ * decay (start 2000, interval 1000, base 0.99); the loss defaults to L2.  Tensor-core
  * precisions need every hidden width == 64 and mlp_dims[0] in {16, 32, 64}.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).  The context
  * owns every buffer it allocates; nv_destroy frees them. */
@@ -121,6 +133,10 @@ nv_status nv_get_params(nv_ctx *ctx, float *params_any);
 nv_status nv_buffer_ptr(nv_ctx *ctx, int which, float **ptr_dev, int64_t *n);
 /* Adam hyper-parameters (App. B lists beta 0.9 / 0.999, eps 1e-15). */
 nv_status nv_set_adam(nv_ctx *ctx, const nv_adam_cfg *cfg);
+/* Loss of nv_train_step (default NV_LOSS_L2): L2 = mean((y - t)^2) with
+ * dL/dy = 2 (y - t) / n; L1 = mean(|y - t|) with dL/dy = sign(y - t) / n (0 at
+ * y == t).  The loss nv_train_step reports follows the choice. */
+nv_status nv_set_loss(nv_ctx *ctx, int loss);
 /* Static loss scale S of the FP16/BF16 backward (default 128 / 1).  A step whose
  * gradient overflows is skipped and S halved, on the device. */
 nv_status nv_set_loss_scale(nv_ctx *ctx, float scale);
@@ -156,8 +172,8 @@ nv_status nv_optimizer_step(nv_ctx *ctx);
  * xyz_dev [n][3] and target_dev [n] may be NULL to skip either output. */
 nv_status nv_sample(const nv_volume *vol, int64_t n, uint64_t seed, uint32_t step, float *xyz_dev,
                     float *target_dev, void *stream);
-/* One training step (Sec. 4): forward, L2 loss mean((y - t)^2), backward,
- * Adam.  Either xyz_any/target_any hold the batch (host or device; host
+/* One training step (Sec. 4): forward, the loss chosen by nv_set_loss
+ * (default L2, mean((y - t)^2)), backward, Adam.  Either xyz_any/target_any hold the batch (host or device; host
  * batches are copied in on the context stream) or both are NULL and the batch
  * is sampled from vol with nv_sample's generator at the context's sample
  * counter.  loss_dev (nullable): the batch loss before the update, FP64. */

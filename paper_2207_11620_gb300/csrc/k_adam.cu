@@ -14,6 +14,8 @@ namespace {
 
 struct AdamHP {
   float lr, b1, b2, eps, l2;
+  int decay_start, decay_interval;
+  float decay_base;
 };
 
 constexpr int kU = 4;  // float4 iterations per thread kept in flight
@@ -40,18 +42,22 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__re
                                               float *__restrict__ m, float *__restrict__ v,
                                               void *__restrict__ shadow, int64_t n, AdamHP hp,
                                               const DevState *__restrict__ ds) {
-  // bias corrections of step t (Kingma & Ba): one FP64 evaluation per CTA
-  __shared__ float s_bc[2];
+  // bias corrections of step t (Kingma & Ba) and the decayed learning rate of
+  // step index t - 1 (App. B): one FP64 evaluation per CTA
+  __shared__ float s_bc[3];
   __shared__ int s_skip;
   if (threadIdx.x == 0) {
     const int t = ds->step + 1;
     s_bc[0] = (float)(1.0 / (1.0 - pow((double)hp.b1, (double)t)));
     s_bc[1] = (float)(1.0 / (1.0 - pow((double)hp.b2, (double)t)));
+    const int k = t - 1;
+    const int d = (k < hp.decay_start || hp.decay_interval <= 0) ? 0 : (k - hp.decay_start) / hp.decay_interval + 1;
+    s_bc[2] = (float)((double)hp.lr * pow((double)hp.decay_base, (double)d));
     s_skip = ds->overflow != 0;
   }
   __syncthreads();
   const bool skip = s_skip != 0;
-  const float inv_bc1 = s_bc[0], inv_bc2 = s_bc[1];
+  const float inv_bc1 = s_bc[0], inv_bc2 = s_bc[1], lr = s_bc[2];
   const int64_t n4 = n >> 2;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,7 +71,7 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__re
     mm = hp.b1 * mm + (1.f - hp.b1) * gg;
     vv = hp.b2 * vv + (1.f - hp.b2) * gg * gg;
     const float mh = mm * inv_bc1, vh = vv * inv_bc2;
-    pp -= hp.lr * mh / (sqrtf(vh) + hp.eps);
+    pp -= lr * mh / (sqrtf(vh) + hp.eps);
   };
   if (skip) {  // an overflowed step: only clear the gradient
     for (int64_t i = t0; i < n4; i += nthr) go[i] = zero;
@@ -140,7 +146,8 @@ __global__ void k_shadow(const float *__restrict__ p, void *__restrict__ shadow,
 }  // namespace
 
 nv_status launch_adam(nv_ctx *c) {
-  AdamHP hp{c->adam.lr, c->adam.beta1, c->adam.beta2, c->adam.eps, c->adam.l2_reg};
+  AdamHP hp{c->adam.lr,          c->adam.beta1,          c->adam.beta2,     c->adam.eps,
+            c->adam.l2_reg,      c->adam.decay_start,    c->adam.decay_interval, c->adam.decay_base};
   int64_t n = c->n_params;
   // one wave of resident CTAs: each thread walks the vector grid-stride
   int per_sm = 0;

@@ -234,8 +234,13 @@ __global__ void __launch_bounds__(kP) k_mlp_f32(NetDesc nd, const float *__restr
     if (valid) {
       if (MODE == MODE_TRAIN) {
         float diff = yv - tgt;
-        local_acc += (double)diff * (double)diff;
-        g = 2.f * diff * a.inv_n;
+        if (a.l1) {
+          local_acc += fabs((double)diff);
+          g = (float)((diff > 0.f) - (diff < 0.f)) * a.inv_n;
+        } else {
+          local_acc += (double)diff * (double)diff;
+          g = 2.f * diff * a.inv_n;
+        }
       } else {
         g = a.in[p];
       }

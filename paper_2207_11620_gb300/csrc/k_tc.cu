@@ -120,7 +120,7 @@ __device__ __forceinline__ bool red_row(float *dst, const float *v, float s) {
       bad = true;
       continue;
     }
-    if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) atomicAdd(reinterpret_cast<float4 *>(dst + j), g);
+    if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) red_v4(dst + j, g.x, g.y, g.z, g.w);
   }
   return bad;
 }
@@ -333,8 +333,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_mlp_tc(NetDesc nd, const float 
       if (valid) {
         if (MODE == MODE_TRAIN) {
           const float diff = yv - tv;
-          if (hh == 0) local_acc += (double)diff * (double)diff;
-          g = 2.f * diff * scale;
+          if (a.l1) {
+            if (hh == 0) local_acc += fabs((double)diff);
+            g = (float)((diff > 0.f) - (diff < 0.f)) * scale;
+          } else {
+            if (hh == 0) local_acc += (double)diff * (double)diff;
+            g = 2.f * diff * scale;
+          }
         } else {
           g = tv * scale;
         }

@@ -135,7 +135,8 @@ extern "C" nv_status nv_create(int L, int F, int log2T, int Nmin, double b, cons
   c->prec = prec;
   c->stream = (cudaStream_t)cuda_stream;
   c->n_params = nd.n_table + nd.n_weights;
-  c->adam = nv_adam_cfg{1e-2f, 0.9f, 0.999f, 1e-15f, 0.0f};
+  c->adam = nv_adam_cfg{1e-2f, 0.9f, 0.999f, 1e-15f, 0.0f, 2000, 1000, 0.99f};
+  c->loss_kind = NV_LOSS_L2;
   if (prec != NV_FP32 && !tc_supported(nd)) {
     delete c;
     return nv_fail(NV_ERR_UNSUPPORTED,
@@ -227,9 +228,17 @@ extern "C" nv_status nv_buffer_ptr(nv_ctx *c, int which, float **ptr, int64_t *n
 extern "C" nv_status nv_set_adam(nv_ctx *c, const nv_adam_cfg *cfg) {
   if (!c || !cfg) return nv_fail(NV_ERR_ARG, "nv_set_adam: NULL argument");
   if (!(cfg->lr >= 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) ||
-      !(cfg->eps >= 0.f) || !(cfg->l2_reg >= 0.f))
+      !(cfg->eps >= 0.f) || !(cfg->l2_reg >= 0.f) || !(cfg->decay_base > 0.f && cfg->decay_base <= 1.f) ||
+      cfg->decay_start < 0)
     return nv_fail(NV_ERR_ARG, "nv_set_adam: hyper-parameters out of range");
   c->adam = *cfg;
+  return NV_OK;
+}
+
+extern "C" nv_status nv_set_loss(nv_ctx *c, int loss) {
+  if (!c) return nv_fail(NV_ERR_ARG, "nv_set_loss: ctx is NULL");
+  if (loss != NV_LOSS_L2 && loss != NV_LOSS_L1) return nv_fail(NV_ERR_ARG, "nv_set_loss: unknown loss %d", loss);
+  c->loss_kind = loss;
   return NV_OK;
 }
 
@@ -337,6 +346,7 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
   a.grads = c->grads;
   a.ds = c->ds;
   a.inv_n = (float)(1.0 / (double)n);
+  a.l1 = c->loss_kind == NV_LOSS_L1;
   if (xyz) {
     if (is_host_ptr(xyz) || is_host_ptr(target)) {
       if (c->batch_cap < n) {

@@ -47,6 +47,7 @@ struct nv_ctx {
   void *shadow;                             // FP16/BF16 copy of params (tensor-core precisions)
   DevState *ds;
   nv_adam_cfg adam;
+  int loss_kind;                            // nv_loss of nv_train_step
   uint32_t sample_counter;                  // Philox step word of sampled batches
   int params_set;
   float *batch;                             // staging for host batches: [cap][3] xyz + [cap] target
@@ -241,6 +242,7 @@ struct MlpArgs {
   uint64_t seed;
   uint32_t sample_step;
   float inv_n;           // TRAIN: 1/n of the batch mean
+  int l1;                // TRAIN: L1 loss (else L2)
 };
 
 // FP32 CUDA-core path

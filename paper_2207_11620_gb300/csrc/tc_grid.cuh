@@ -185,17 +185,30 @@ __device__ __forceinline__ void gather_levels(const uint16_t *__restrict__ shado
   }
 }
 
+// Fire-and-forget FP32 reductions (no value returned, so the issuing thread
+// never waits for L2): 1, 2 or 4 floats at a 4-, 8- or 16-byte aligned address.
+__device__ __forceinline__ void red_f32(float *p, float a) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(a) : "memory");
+}
+__device__ __forceinline__ void red_v2(float *p, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void red_v4(float *p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
 template <int F>
 __device__ __forceinline__ void red_entry(float *p, const float *g) {
   if constexpr (F == 1) {
-    atomicAdd(p, g[0]);
+    red_f32(p, g[0]);
   } else if constexpr (F == 2) {
-    atomicAdd(reinterpret_cast<float2 *>(p), make_float2(g[0], g[1]));
+    red_v2(p, g[0], g[1]);
   } else if constexpr (F == 4) {
-    atomicAdd(reinterpret_cast<float4 *>(p), make_float4(g[0], g[1], g[2], g[3]));
+    red_v4(p, g[0], g[1], g[2], g[3]);
   } else {
-    atomicAdd(reinterpret_cast<float4 *>(p), make_float4(g[0], g[1], g[2], g[3]));
-    atomicAdd(reinterpret_cast<float4 *>(p) + 1, make_float4(g[4], g[5], g[6], g[7]));
+    red_v4(p, g[0], g[1], g[2], g[3]);
+    red_v4(p + 4, g[4], g[5], g[6], g[7]);
   }
 }
 
@@ -226,8 +239,9 @@ __device__ __forceinline__ void scatter_level(float *gt, uint32_t mask, float N,
     }
     if (F == 2 && even) {
       const bool odd0 = (h0 & 1u) != 0;
-      float4 v = odd0 ? make_float4(g1[0], g1[1], g0[0], g0[1]) : make_float4(g0[0], g0[1], g1[0], g1[1]);
-      atomicAdd(reinterpret_cast<float4 *>(gt + (size_t)(h0 & ~1u) * 2), v);
+      float *dst = gt + (size_t)(h0 & ~1u) * 2;
+      if (odd0) red_v4(dst, g1[0], g1[1], g0[0], g0[1]);
+      else red_v4(dst, g0[0], g0[1], g1[0], g1[1]);
     } else {
       const uint32_t h1 = ((uint32_t)(cx + 1) ^ hy) & mask;
       red_entry<F>(gt + (size_t)h0 * F, g0);

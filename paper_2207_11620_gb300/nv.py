@@ -49,7 +49,8 @@ class Macrocells(C.Structure):
 
 class AdamCfg(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("l2_reg", C.c_float)]
+                ("l2_reg", C.c_float), ("decay_start", C.c_int), ("decay_interval", C.c_int),
+                ("decay_base", C.c_float)]
 
 
 EXPORTS = {
@@ -63,6 +64,7 @@ EXPORTS = {
     "nv_buffer_ptr": ([C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)], C.c_int),
     "nv_set_adam": ([C.c_void_p, C.POINTER(AdamCfg)], C.c_int),
     "nv_set_loss_scale": ([C.c_void_p, C.c_float], C.c_int),
+    "nv_set_loss": ([C.c_void_p, C.c_int], C.c_int),
     "nv_get_step": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float)], C.c_int),
     "nv_hash_indices": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "nv_encode": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
@@ -236,9 +238,14 @@ class NeuralVolume:
             self._param_view = self.buffer("params").requires_grad_(True)
         return self._param_view
 
-    def set_adam(self, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-15, l2_reg=0.0):
-        cfg = AdamCfg(lr, beta1, beta2, eps, l2_reg)
+    def set_adam(self, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-15, l2_reg=0.0, decay_start=2000,
+                 decay_interval=1000, decay_base=0.99):
+        cfg = AdamCfg(lr, beta1, beta2, eps, l2_reg, decay_start, decay_interval, decay_base)
         _check(lib().nv_set_adam(self._h, C.byref(cfg)))
+
+    def set_loss(self, loss):
+        """'l2' (default) or 'l1'."""
+        _check(lib().nv_set_loss(self._h, {"l2": 0, "l1": 1}[loss]))
 
     def set_loss_scale(self, s):
         _check(lib().nv_set_loss_scale(self._h, float(s)))
