@@ -198,6 +198,72 @@ __device__ __forceinline__ void red_v4(float *p, float a, float b, float c, floa
                : "memory");
 }
 
+// Entry k (0..3) of a 16-byte group of four 4-byte entries.
+__device__ __forceinline__ uint32_t pick4(const uint4 &g, uint32_t k) {
+  const uint32_t lo = (k & 1u) ? g.y : g.x, hi = (k & 1u) ? g.w : g.z;
+  return (k & 2u) ? hi : lo;
+}
+
+// A-1..A-3 for G consecutive levels of an F = 2 table with 16-bit features
+// (4-byte entries).  The x-corners of a cell hash to h0 = cx ^ hy and h1 =
+// (cx + 1) ^ hy (the x prime is 1), so h0 ^ h1 = cx ^ (cx + 1): 1 for even cx,
+// 3 for cx = 1 mod 4, 7 or more otherwise.  One aligned 16-byte load of the
+// four entries around h0 therefore serves both corners in three cells of four,
+// and only cx = 3 mod 4 needs a second load: 5 loads per point and level on
+// average instead of 6 with pairs.  Every load of the G levels is issued before
+// any is consumed.
+template <bool BF, int G>
+__device__ __forceinline__ void gather_levels_f2(const uint16_t *__restrict__ shadow, const NetDesc &nd, int l0,
+                                                 float x, float y, float z, float *out) {
+  const uint32_t mask = nd.T - 1;
+  uint4 grp[G][4];
+  uint32_t sg[G][4];
+  uint32_t sel[G];  // per corner row q: bits 8q..8q+7 = h0 & 3 | (h1 & 3) << 2 | (same group) << 4
+  float wxs[G], wys[G], wzs[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int l = l0 + g;
+    int cx, cy, cz;
+    const float N = (float)nd.res[l];
+    nv_cell(x, N, cx, wxs[g]);
+    nv_cell(y, N, cy, wys[g]);
+    nv_cell(z, N, cz, wzs[g]);
+    const uint16_t *tab = shadow + (size_t)l * nd.T * 2;
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dy = q & 1, dz = q >> 1;
+      const uint32_t hy = ((uint32_t)(cy + dy) * 2654435761u) ^ ((uint32_t)(cz + dz) * 805459861u);
+      const uint32_t h0 = ((uint32_t)cx ^ hy) & mask;
+      const uint32_t h1 = ((uint32_t)(cx + 1) ^ hy) & mask;
+      const bool same = (h0 >> 2) == (h1 >> 2);
+      s |= ((h0 & 3u) | ((h1 & 3u) << 2) | ((same ? 1u : 0u) << 4)) << (8 * q);
+      grp[g][q] = __ldg(reinterpret_cast<const uint4 *>(tab + (size_t)(h0 & ~3u) * 2));
+      if (!same) sg[g][q] = __ldg(reinterpret_cast<const uint32_t *>(tab + (size_t)h1 * 2));
+    }
+    sel[g] = s;
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dy = q & 1, dz = q >> 1;
+      const uint32_t s = sel[g] >> (8 * q);
+      const uint32_t e0 = pick4(grp[g][q], s & 3u);
+      const uint32_t e1 = (s & 16u) ? pick4(grp[g][q], (s >> 2) & 3u) : sg[g][q];
+      const float2 v0 = Half<BF>::unpack(*reinterpret_cast<const typename Half<BF>::T2 *>(&e0));
+      const float2 v1 = Half<BF>::unpack(*reinterpret_cast<const typename Half<BF>::T2 *>(&e1));
+      const float wyz = (dy ? wys[g] : 1.f - wys[g]) * (dz ? wzs[g] : 1.f - wzs[g]);
+      const float w0 = (1.f - wxs[g]) * wyz, w1 = wxs[g] * wyz;
+      a0 += w0 * v0.x + w1 * v1.x;
+      a1 += w0 * v0.y + w1 * v1.y;
+    }
+    out[2 * g] = a0;
+    out[2 * g + 1] = a1;
+  }
+}
+
 template <int F>
 __device__ __forceinline__ void red_entry(float *p, const float *g) {
   if constexpr (F == 1) {
