@@ -425,19 +425,24 @@ def _render_setup(nv, I, torch, cfg, vt):
     return lut, mu, opts
 
 
+def _median_frame_ms(torch, frames, fn):
+    """Median device time of `frames` calls of fn (CUDA events around each), after one warm-up call."""
+    img = fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+    for a, b in ev:
+        a.record()
+        img = fn()
+        b.record()
+    torch.cuda.synchronize()
+    return img, statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
 def _time_render(r, torch, frames, **kw):
-    r.render(**kw)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(frames):
-        img = r.render(**kw)
-    e1.record()
-    torch.cuda.synchronize()
-    return img, e0.elapsed_time(e1) / frames
+    return _median_frame_ms(torch, frames, lambda: r.render(**kw))
 
 
-def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=5):
+def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
     """Config 3: 512^3 volume, T2^21 network trained with config 2's recipe, 1080p
     perspective march (0.5 voxel, 16^3 macrocells, ET 0.99) with FP16 and BF16
     inference; PSNR of each neural image against the raw-volume image."""
@@ -468,10 +473,18 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=5):
         img, ms = _time_render(r, torch, frames, cam=cam, lut=lut, opts=opts, net=net, mc=mc)
         it, ns = r.stats()
         mse = nv.image_mse(img, raw).item()
+        # the same frame by in-shader inference (Sec. 5.1): one megakernel
+        sam = torch.zeros(1, dtype=torch.int64, device="cuda")
+        is_img = torch.empty_like(img)
+        is_img, is_ms = _median_frame_ms(
+            torch, frames, lambda: nv.render_inshader(net, cam, lut, opts, mc=mc, out=is_img, samples=sam))
         out[prec] = {"train_steps": steps, "train_ms_per_step": e0.elapsed_time(e1) / steps,
                      "frame_ms": ms, "samples_per_frame": ns, "iterations": it,
                      "decoded_samples_per_s": ns / (ms / 1e3), "image_psnr_db": _psnr(mse),
-                     "volume_psnr_db": _psnr(net.volume_mse(vt).item())}
+                     "volume_psnr_db": _psnr(net.volume_mse(vt).item()),
+                     "inshader": {"frame_ms": is_ms, "samples_per_frame": int(sam.item()),
+                                  "max_abs_diff_vs_streaming": float((is_img - img).abs().max().item()),
+                                  "streaming_speedup": is_ms / ms}}
         net.close()
     r.close()
     del vt
@@ -590,10 +603,13 @@ def run_extras(args):
                      ("cfg4_inloop", extra_cfg4_inloop), ("cfg5_ooc", extra_cfg5_ooc)):
         if name not in args.extras:
             continue
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
         try:
             out[name] = fn(nv, I, CF, torch)
         except Exception as e:  # report and keep the main line
             out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        out[name]["clocks"] = clocks.stop()
     return out
 
 

@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "nv_internal.cuh"
+#include "render_common.cuh"
 
 namespace {
 
@@ -123,18 +124,7 @@ __global__ void k_raygen(nv_camera cam, float *ray, int *next_k, int64_t cap, in
   }
 }
 
-struct McView {
-  const float *mu;  // nullptr: no skipping
-  int ncx, ncy, ncz;
-  float sx, sy, sz;  // cells per unit length along each axis (n / cell)
-};
-
-// Next K sample positions of each live ray (A-12).  Sample k sits at
-// t_k = t0 + (k + 1/2) step (FP32, the same operations as the oracle).  A
-// sample inside a transparent macrocell is skipped; the walk jumps to two
-// samples before the cell's exit so every sample near a cell face is still
-// tested on its own, which makes the skipped set exactly the per-sample
-// definition.
+// Next K sample positions of each live ray (A-12, march_step).
 __global__ void k_coords(const float *__restrict__ ray, int *next_k, int64_t cap, const int *count, int K,
                          float step, McView mc, float *coords, int *nvalid) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,33 +134,11 @@ __global__ void k_coords(const float *__restrict__ ray, int *next_k, int64_t cap
   const float t0 = ray[R_T0 * cap + i], t1 = ray[R_T1 * cap + i];
   int k = next_k[i];
   int cnt = 0;
+  float pos[3];
   while (cnt < K) {
-    const float tk = __fadd_rn(t0, __fmul_rn(__fadd_rn((float)k, 0.5f), step));
-    if (!(tk < t1)) break;
-    float pos[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) pos[a] = __fadd_rn(o[a], __fmul_rn(tk, d[a]));
-    if (mc.mu) {
-      int cx = min(max((int)floorf(__fmul_rn(pos[0], mc.sx)), 0), mc.ncx - 1);
-      int cy = min(max((int)floorf(__fmul_rn(pos[1], mc.sy)), 0), mc.ncy - 1);
-      int cz = min(max((int)floorf(__fmul_rn(pos[2], mc.sz)), 0), mc.ncz - 1);
-      if (__ldg(mc.mu + ((int64_t)cz * mc.ncy + cy) * mc.ncx + cx) == 0.0f) {
-        // exit distance of this cell along the ray (approximate; only used to jump)
-        const int cc[3] = {cx, cy, cz};
-        const float sc[3] = {mc.sx, mc.sy, mc.sz};
-        float texit = __int_as_float(0x7f800000);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          if (d[a] > 0.f) texit = fminf(texit, ((float)(cc[a] + 1) / sc[a] - o[a]) / d[a]);
-          else if (d[a] < 0.f) texit = fminf(texit, ((float)cc[a] / sc[a] - o[a]) / d[a]);
-        }
-        float kf = ceilf((texit - t0) / step - 0.5f) - 2.0f;
-        int kj = k + 1;
-        if (kf > (float)kj) kj = (kf < 2.0e9f) ? (int)kf : 2000000000;
-        k = kj;
-        continue;
-      }
-    }
+    const int m = march_step(o, d, t0, t1, step, mc, k, pos);
+    if (m == kMarchEnd) break;
+    if (m == kMarchSkip) continue;
     float *dst = coords + (i * K + cnt) * 3;
     dst[0] = pos[0];
     dst[1] = pos[1];
@@ -216,22 +184,7 @@ __global__ void k_composite(const float *__restrict__ ray, const int *__restrict
     nv = nvalid[i];
     bool done = false;
     for (int j = 0; j < nv; ++j) {
-      const float v = values[i * K + j];
-      const float u = __fmul_rn(fminf(fmaxf(v, 0.f), 1.f), 255.0f);
-      const int e = min((int)floorf(u), 254);
-      const float w = u - (float)e;
-      const float4 l0 = __ldg(reinterpret_cast<const float4 *>(lut) + e);
-      const float4 l1 = __ldg(reinterpret_cast<const float4 *>(lut) + e + 1);
-      const float r = l0.x + w * (l1.x - l0.x), g = l0.y + w * (l1.y - l0.y), b = l0.z + w * (l1.z - l0.z);
-      const float al = l0.w + w * (l1.w - l0.w);
-      // a' = 1 - (1 - a)^e, as -expm1(e log1p(-a)) to keep small opacities accurate
-      const float ac = (alpha_exp == 1.0f) ? al : -expm1f(alpha_exp * log1pf(-al));
-      const float tr = (1.0f - ca) * ac;
-      cr += tr * r;
-      cg += tr * g;
-      cb += tr * b;
-      ca += tr;
-      if (ca >= et) {
+      if (composite_one(values[i * K + j], lut, alpha_exp, et, cr, cg, cb, ca)) {
         done = true;
         break;
       }
@@ -329,16 +282,7 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
 
-  McView mv{nullptr, 1, 1, 1, 0.f, 0.f, 0.f};
-  if (mc) {
-    mv.mu = mc->mu_max_dev;
-    mv.ncx = (mc->nx + mc->cell - 1) / mc->cell;
-    mv.ncy = (mc->ny + mc->cell - 1) / mc->cell;
-    mv.ncz = (mc->nz + mc->cell - 1) / mc->cell;
-    mv.sx = (float)mc->nx / (float)mc->cell;
-    mv.sy = (float)mc->ny / (float)mc->cell;
-    mv.sz = (float)mc->nz / (float)mc->cell;
-  }
+  const McView mv = mc_view(mc);
   // every iteration consumes at least one sample of each live ray, or ends it
   const int64_t max_iter = (int64_t)std::ceil(1.7320509 / (double)o.step / (double)K) + 4;
   const int R = 4;  // iterations in flight before the host waits for a count
@@ -355,8 +299,10 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   int cur = 0;
   while (bound > 0 && issued < max_iter) {
     const int nxt = cur ^ 1;
+    int tk = net ? prof_begin(net) : -1;
     k_coords<<<blocks_for(bound, 128), 128, 0, st>>>(r->ray[cur], r->next_k[cur], cap, &r->counters[cur], K,
                                                      o.step, mv, r->coords, r->nvalid);
+    if (net) prof_end(net, NV_K_OTHER, tk);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_coords launch")) != NV_OK) break;
     if (net) {
       MlpArgs a{};
@@ -375,9 +321,11 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
       s = nv_cuda_check(e, "cudaMemsetAsync");
       break;
     }
+    tk = net ? prof_begin(net) : -1;
     k_composite<<<blocks_for(bound, 128), 128, 0, st>>>(
         r->ray[cur], r->next_k[cur], cap, &r->counters[cur], r->values, r->nvalid, K, lut, o.alpha_exp, o.et,
         r->ray[nxt], r->next_k[nxt], &r->counters[nxt], out, reinterpret_cast<unsigned long long *>(r->d_samples));
+    if (net) prof_end(net, NV_K_RENDER, tk);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_composite launch")) != NV_OK) break;
     const int slot = (int)(issued % R);
     cudaMemcpyAsync(&r->h_count[slot], &r->counters[nxt], sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -427,16 +375,7 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
   k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r.ray[0], r.next_k[0], cap, &r.counters[0], out);
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
-  McView mv{nullptr, 1, 1, 1, 0.f, 0.f, 0.f};
-  if (mc) {
-    mv.mu = mc->mu_max_dev;
-    mv.ncx = (mc->nx + mc->cell - 1) / mc->cell;
-    mv.ncy = (mc->ny + mc->cell - 1) / mc->cell;
-    mv.ncz = (mc->nz + mc->cell - 1) / mc->cell;
-    mv.sx = (float)mc->nx / (float)mc->cell;
-    mv.sy = (float)mc->ny / (float)mc->cell;
-    mv.sz = (float)mc->nz / (float)mc->cell;
-  }
+  const McView mv = mc_view(mc);
   const int64_t max_iter = (int64_t)std::ceil(1.7320509 / (double)o.step / (double)K) + 4;
   int live = 0;
   if ((e = cudaMemcpyAsync(&live, &r.counters[0], sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

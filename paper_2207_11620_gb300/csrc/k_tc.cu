@@ -96,17 +96,6 @@ struct SpanCheck {
 };
 static_assert(SpanCheck<16>::ok && SpanCheck<32>::ok && SpanCheck<64>::ok, "operand spans");
 
-// Store 8 consecutive K values (one 16-byte core-matrix row) of row r.
-template <bool BF>
-__device__ __forceinline__ void st_row8(uint8_t *base, int r, int c, int K, const float *v) {
-  uint4 u;
-  u.x = pack16x2<BF>(v[0], v[1]);
-  u.y = pack16x2<BF>(v[2], v[3]);
-  u.z = pack16x2<BF>(v[4], v[5]);
-  u.w = pack16x2<BF>(v[6], v[7]);
-  *reinterpret_cast<uint4 *>(base + tile_off(r, c * 8, K)) = u;
-}
-
 // Add n scaled values to 16-byte aligned dst with n / 4 vector reductions,
 // skipping all-zero groups; returns whether any value is not finite (that
 // group is then left out).
@@ -125,9 +114,6 @@ __device__ __forceinline__ bool red_row(float *dst, const float *v, float s) {
   return bad;
 }
 
-__device__ __forceinline__ uint64_t desc_k(uint32_t saddr, int K) {  // K-major [rows][K]
-  return tc::smem_desc(saddr, 128, (uint32_t)K * 16);
-}
 __device__ __forceinline__ uint64_t desc_mn(uint32_t saddr, int Kphys) {  // MN-major view of [pts][Kphys]
   const uint32_t mn = 128, kk = (uint32_t)Kphys * 16;
   return kMnLboIsMn ? tc::smem_desc(saddr, mn, kk) : tc::smem_desc(saddr, kk, mn);

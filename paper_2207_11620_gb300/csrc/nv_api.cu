@@ -466,6 +466,23 @@ extern "C" nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw
   return render_impl(r, net, raw, *cam, lut, mc, *opts, rgba);
 }
 
+extern "C" nv_status nv_render_inshader(nv_ctx *net, const nv_camera *cam, const float *lut,
+                                        const nv_macrocells *mc, const nv_render_opts *opts, float *rgba,
+                                        int64_t *samples_dev) {
+  if (!net || !cam || !lut || !opts || !rgba) return nv_fail(NV_ERR_ARG, "nv_render_inshader: NULL argument");
+  if (!net->params_set) return nv_fail(NV_ERR_STATE, "nv_render_inshader: network parameters never set");
+  if (cam->width < 1 || cam->height < 1)
+    return nv_fail(NV_ERR_ARG, "nv_render_inshader: image %dx%d", cam->width, cam->height);
+  if ((int64_t)cam->width * cam->height > ((int64_t)1 << 31) - 256)
+    return nv_fail(NV_ERR_ARG, "nv_render_inshader: image too large");
+  if (!(opts->step > 0.f) || !(opts->alpha_exp > 0.f) || !(opts->et > 0.f))
+    return nv_fail(NV_ERR_ARG, "nv_render_inshader: step, alpha_exp and et must be > 0");
+  if (mc && (!mc->mu_max_dev || mc->cell < 1 || mc->nx < 1 || mc->ny < 1 || mc->nz < 1))
+    return nv_fail(NV_ERR_ARG, "nv_render_inshader: bad macrocell grid");
+  if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render_inshader: tan_half_fovy < 0");
+  return render_inshader(net, *cam, lut, mc, *opts, rgba, reinterpret_cast<unsigned long long *>(samples_dev));
+}
+
 extern "C" nv_status nv_render_stats(nv_renderer *r, int *iterations, int64_t *samples) {
   if (!r) return nv_fail(NV_ERR_ARG, "nv_render_stats: renderer is NULL");
   NV_CUDA(cudaDeviceSynchronize(), "nv_render_stats: sync");

@@ -270,6 +270,10 @@ nv_status launch_macrocells(const nv_volume &v, int cell, const float *lut, floa
                             float *mu, cudaStream_t s);
 nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera &cam,
                       const float *lut, const nv_macrocells *mc, const nv_render_opts &o, float *rgba);
+// In-shader ray march (k_inshader.cu); samples (nullable, device) counts the
+// evaluated samples.
+nv_status render_inshader(nv_ctx *c, const nv_camera &cam, const float *lut, const nv_macrocells *mc,
+                          const nv_render_opts &o, float *rgba, unsigned long long *samples);
 nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const nv_camera &cam, const float *lut,
                                const nv_macrocells *mc, const nv_render_opts &o, float *rgba, cudaStream_t st);
 nv_status launch_image_mse(const float *a, const float *b, int64_t n, double *out, cudaStream_t s);

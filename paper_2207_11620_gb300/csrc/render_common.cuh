@@ -1,0 +1,87 @@
+// render_common.cuh -- per-ray pieces of the emission-absorption ray march
+// shared by the sample-streaming kernels (k_render.cu) and the in-shader
+// megakernel (k_inshader.cu), so both take the same samples and composite
+// them with the same arithmetic.
+#pragma once
+
+#include "nv_internal.cuh"
+
+struct McView {
+  const float *mu;  // nullptr: no skipping
+  int ncx, ncy, ncz;
+  float sx, sy, sz;  // cells per unit length along each axis (n / cell)
+};
+
+inline McView mc_view(const nv_macrocells *mc) {
+  McView mv{nullptr, 1, 1, 1, 0.f, 0.f, 0.f};
+  if (mc) {
+    mv.mu = mc->mu_max_dev;
+    mv.ncx = (mc->nx + mc->cell - 1) / mc->cell;
+    mv.ncy = (mc->ny + mc->cell - 1) / mc->cell;
+    mv.ncz = (mc->nz + mc->cell - 1) / mc->cell;
+    mv.sx = (float)mc->nx / (float)mc->cell;
+    mv.sy = (float)mc->ny / (float)mc->cell;
+    mv.sz = (float)mc->nz / (float)mc->cell;
+  }
+  return mv;
+}
+
+// A-12, one step of the walk along a ray.  Sample k sits at t_k = t0 + (k +
+// 1/2) step (FP32, the same operations as the oracle).  A sample inside a
+// transparent macrocell (mu_max == 0, Sec. 5.3) is skipped: the walk jumps to
+// two samples before the cell's exit, so every sample near a cell face is
+// still tested on its own, which makes the skipped set exactly the per-sample
+// definition.  Returns kMarchEnd once t_k >= t1, kMarchSkip after moving k
+// past a transparent stretch, kMarchSample with pos = the position of sample k
+// (k unchanged).  Callers loop one step per iteration, so the lanes of a warp
+// that skip and the lanes that take samples advance together.
+enum { kMarchEnd = 0, kMarchSample = 1, kMarchSkip = 2 };
+
+__device__ __forceinline__ int march_step(const float *o, const float *d, float t0, float t1, float step,
+                                          const McView &mc, int &k, float *pos) {
+  const float tk = __fadd_rn(t0, __fmul_rn(__fadd_rn((float)k, 0.5f), step));
+  if (!(tk < t1)) return kMarchEnd;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pos[a] = __fadd_rn(o[a], __fmul_rn(tk, d[a]));
+  if (!mc.mu) return kMarchSample;
+  const int cx = min(max((int)floorf(__fmul_rn(pos[0], mc.sx)), 0), mc.ncx - 1);
+  const int cy = min(max((int)floorf(__fmul_rn(pos[1], mc.sy)), 0), mc.ncy - 1);
+  const int cz = min(max((int)floorf(__fmul_rn(pos[2], mc.sz)), 0), mc.ncz - 1);
+  if (__ldg(mc.mu + ((int64_t)cz * mc.ncy + cy) * mc.ncx + cx) != 0.0f) return kMarchSample;
+  // exit distance of this cell along the ray (approximate; only used to jump)
+  const int cc[3] = {cx, cy, cz};
+  const float sc[3] = {mc.sx, mc.sy, mc.sz};
+  float texit = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] > 0.f) texit = fminf(texit, ((float)(cc[a] + 1) / sc[a] - o[a]) / d[a]);
+    else if (d[a] < 0.f) texit = fminf(texit, ((float)cc[a] / sc[a] - o[a]) / d[a]);
+  }
+  const float kf = ceilf((texit - t0) / step - 0.5f) - 2.0f;
+  int kj = k + 1;
+  if (kf > (float)kj) kj = (kf < 2.0e9f) ? (int)kf : 2000000000;
+  k = kj;
+  return kMarchSkip;
+}
+
+// A-14 for one sample value v: transfer function (linear between the 256 LUT
+// entries), opacity correction a' = 1 - (1 - a)^e, front-to-back compositing.
+// Returns true once the accumulated opacity reaches et (early termination).
+__device__ __forceinline__ bool composite_one(float v, const float *__restrict__ lut, float alpha_exp, float et,
+                                              float &cr, float &cg, float &cb, float &ca) {
+  const float u = __fmul_rn(fminf(fmaxf(v, 0.f), 1.f), 255.0f);
+  const int e = min((int)floorf(u), 254);
+  const float w = u - (float)e;
+  const float4 l0 = __ldg(reinterpret_cast<const float4 *>(lut) + e);
+  const float4 l1 = __ldg(reinterpret_cast<const float4 *>(lut) + e + 1);
+  const float r = l0.x + w * (l1.x - l0.x), g = l0.y + w * (l1.y - l0.y), b = l0.z + w * (l1.z - l0.z);
+  const float al = l0.w + w * (l1.w - l0.w);
+  // a' = 1 - (1 - a)^e, as -expm1(e log1p(-a)) to keep small opacities accurate
+  const float ac = (alpha_exp == 1.0f) ? al : -expm1f(alpha_exp * log1pf(-al));
+  const float tr = (1.0f - ca) * ac;
+  cr += tr * r;
+  cg += tr * g;
+  cb += tr * b;
+  ca += tr;
+  return ca >= et;
+}

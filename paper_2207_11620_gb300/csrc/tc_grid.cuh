@@ -5,6 +5,7 @@
 #pragma once
 
 #include "nv_internal.cuh"
+#include "tc_ptx.cuh"
 
 // Where the points of a launch come from.
 struct PointSrc {
@@ -81,6 +82,23 @@ template <bool BF>
 __device__ __forceinline__ uint32_t pack16x2(float a, float b) {
   typename Half<BF>::T2 h = Half<BF>::pack(a, b);
   return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Store 8 consecutive K values (one 16-byte core-matrix row) of row r.
+template <bool BF>
+__device__ __forceinline__ void st_row8(uint8_t *base, int r, int c, int K, const float *v) {
+  uint4 u;
+  u.x = pack16x2<BF>(v[0], v[1]);
+  u.y = pack16x2<BF>(v[2], v[3]);
+  u.z = pack16x2<BF>(v[4], v[5]);
+  u.w = pack16x2<BF>(v[6], v[7]);
+  *reinterpret_cast<uint4 *>(base + tile_off(r, c * 8, K)) = u;
+}
+
+// Shared-memory descriptor of a K-major [rows][K] no-swizzle operand: the next
+// 8 K values are 128 B on, the next 8 rows K * 16 B on.
+__device__ __forceinline__ uint64_t desc_k(uint32_t saddr, int K) {
+  return tc::smem_desc(saddr, 128, (uint32_t)K * 16);
 }
 
 template <int F>

@@ -65,6 +65,8 @@ EXPORTS = {
     "nv_set_adam": ([C.c_void_p, C.POINTER(AdamCfg)], C.c_int),
     "nv_set_loss_scale": ([C.c_void_p, C.c_float], C.c_int),
     "nv_set_loss": ([C.c_void_p, C.c_int], C.c_int),
+    "nv_render_inshader": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+                           C.c_int),
     "nv_get_step": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float)], C.c_int),
     "nv_hash_indices": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "nv_encode": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
@@ -382,6 +384,27 @@ class Renderer:
         it, sm = C.c_int(), C.c_int64()
         _check(lib().nv_render_stats(self._h, C.byref(it), C.byref(sm)))
         return it.value, sm.value
+
+
+def render_inshader(net: NeuralVolume, cam: dict, lut, opts: dict, mc: tuple | None = None, out=None,
+                    samples=None):
+    """In-shader ray march of `net` (nv_render_inshader): RGBA image [H, W, 4].
+    mc as Renderer.render; samples (optional int64 CUDA tensor of 1) receives the
+    evaluated sample count."""
+    c = camera(cam)
+    if out is None:
+        out = torch.empty((c.height, c.width, 4), dtype=torch.float32, device="cuda")
+    o = RenderOpts(float(opts["step"]), float(opts.get("alpha_exp", 1.0)), float(opts.get("et", 0.99)),
+                   int(opts.get("K", 1)))
+    mp = None
+    if mc is not None:
+        mu, cell, shape = mc
+        m = Macrocells(_dev(mu, name="mu_max").value, int(cell), int(shape[2]), int(shape[1]), int(shape[0]))
+        mp = C.byref(m)
+    sp = _dev(samples, torch.int64, "samples") if samples is not None else None
+    _check(lib().nv_render_inshader(net.handle, C.byref(c), _dev(lut, name="lut"), mp, C.byref(o),
+                                    _dev(out, name="out"), sp))
+    return out
 
 
 def image_mse(a, b, out=None):
