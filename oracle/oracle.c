@@ -421,6 +421,20 @@ void or_trilinear(const float *vol, int nx, int ny, int nz, const float *xyz, in
  * largest opacity mu_max the transfer function reaches on that range: the
  * maximum LUT alpha over entries floor(255*min) .. ceil(255*max) (FP32
  * products, the index decision). */
+/* Largest LUT opacity over the entries a value range [vmin, vmax] can reach
+ * (Sec. 5.3): entries floor(255 vmin) .. ceil(255 vmax) after clamping to
+ * [0, 1], FP32 products (the index decision).  An empty range (vmin > vmax,
+ * e.g. +inf / -inf) covers no entry and gives 0. */
+static float or_mu_of_range(float vmin, float vmax, const float *lut) {
+  float a0 = vmin < 0.0f ? 0.0f : (vmin > 1.0f ? 1.0f : vmin);
+  float a1 = vmax < 0.0f ? 0.0f : (vmax > 1.0f ? 1.0f : vmax);
+  int e0 = (int)floorf(a0 * 255.0f), e1 = (int)ceilf(a1 * 255.0f);
+  if (e1 > 255) e1 = 255;
+  float mu = 0.0f;
+  for (int e = e0; e <= e1; ++e) if (lut[4 * e + 3] > mu) mu = lut[4 * e + 3];
+  return mu;
+}
+
 void or_macrocells(const float *vol, int nx, int ny, int nz, int Ng, const float *lut,
                    float *minmax, float *mumax) {
   int ncx = (nx + Ng - 1) / Ng, ncy = (ny + Ng - 1) / Ng, ncz = (nz + Ng - 1) / Ng;
@@ -445,14 +459,36 @@ void or_macrocells(const float *vol, int nx, int ny, int nz, int Ng, const float
         int64_t c = ((int64_t)cz * ncy + cy) * ncx + cx;
         minmax[2 * c] = vmin;
         minmax[2 * c + 1] = vmax;
-        float a0 = vmin < 0.0f ? 0.0f : (vmin > 1.0f ? 1.0f : vmin);
-        float a1 = vmax < 0.0f ? 0.0f : (vmax > 1.0f ? 1.0f : vmax);
-        int e0 = (int)floorf(a0 * 255.0f), e1 = (int)ceilf(a1 * 255.0f);
-        if (e1 > 255) e1 = 255;
-        float mu = 0.0f;
-        for (int e = e0; e <= e1; ++e) if (lut[4 * e + 3] > mu) mu = lut[4 * e + 3];
-        mumax[c] = mu;
+        mumax[c] = or_mu_of_range(vmin, vmax, lut);
       }
+}
+
+/* Online macrocells (Sec. 5.3): the value ranges are grown from the training
+ * samples themselves instead of a pass over the voxels.  Sample i at position
+ * xyz[i] (unit box) with value val[i] widens the range of the macrocell that
+ * contains the position, cell index floor(fl32(x * fl32(n / Ng))) per axis
+ * clamped to the grid -- the mapping the ray march uses to look cells up.
+ * minmax [nc][2] is updated in place (start from +inf / -inf: empty). */
+void or_mc_online_update(const float *xyz, const float *val, int64_t n, int nx, int ny, int nz, int Ng,
+                         float *minmax) {
+  int nc[3] = {(nx + Ng - 1) / Ng, (ny + Ng - 1) / Ng, (nz + Ng - 1) / Ng};
+  float sc[3] = {(float)nx / (float)Ng, (float)ny / (float)Ng, (float)nz / (float)Ng};
+  for (int64_t i = 0; i < n; ++i) {
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+      c[a] = (int)floorf(xyz[3 * i + a] * sc[a]);
+      if (c[a] < 0) c[a] = 0;
+      if (c[a] > nc[a] - 1) c[a] = nc[a] - 1;
+    }
+    int64_t k = ((int64_t)c[2] * nc[1] + c[1]) * nc[0] + c[0];
+    if (val[i] < minmax[2 * k]) minmax[2 * k] = val[i];
+    if (val[i] > minmax[2 * k + 1]) minmax[2 * k + 1] = val[i];
+  }
+}
+
+/* mu_max of every macrocell from its value range (or_mu_of_range). */
+void or_mc_mu(const float *minmax, int64_t ncells, const float *lut, float *mumax) {
+  for (int64_t c = 0; c < ncells; ++c) mumax[c] = or_mu_of_range(minmax[2 * c], minmax[2 * c + 1], lut);
 }
 
 /* ----------------------------------------------------------- renderer -- */

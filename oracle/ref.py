@@ -88,6 +88,8 @@ def lib():
         L.or_sample_points.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int64, _f32p]
         L.or_trilinear.argtypes = [_f32p, C.c_int, C.c_int, C.c_int, _f32p, C.c_int64, _f64p]
         L.or_macrocells.argtypes = [_f32p, C.c_int, C.c_int, C.c_int, C.c_int, _f32p, _f32p, _f32p]
+        L.or_mc_online_update.argtypes = [_f32p, _f32p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _f32p]
+        L.or_mc_mu.argtypes = [_f32p, C.c_int64, _f32p, _f32p]
         L.or_render_pixels.argtypes = [C.POINTER(_Cam), _f32p, C.POINTER(_Opts), C.c_int, C.c_int,
                                        C.c_int, C.c_int, _i32p, _i32p, C.c_int, C.c_void_p,
                                        C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, _i64p,
@@ -285,6 +287,30 @@ def macrocells(vol, cell, lut):
     mu = np.zeros(nc, dtype=np.float32)
     lib().or_macrocells(vol, nx, ny, nz, cell, _f32(lut), mm, mu)
     return mm, mu
+
+
+def mc_online_empty(shape, cell):
+    """Empty online value ranges [ncz, ncy, ncx, 2] (+inf, -inf) for a volume of `shape` (nz, ny, nx)."""
+    nc = tuple(-(-n // cell) for n in shape)
+    mm = np.empty(nc + (2,), dtype=np.float32)
+    mm[..., 0] = np.inf
+    mm[..., 1] = -np.inf
+    return mm
+
+
+def mc_online_update(minmax, xyz, val, shape, cell):
+    """Grow the ranges `minmax` (in place) with samples xyz [n, 3] of values val [n]."""
+    xyz, val = _f32(xyz), _f32(val)
+    assert minmax.dtype == np.float32 and minmax.flags.c_contiguous
+    nz, ny, nx = shape
+    lib().or_mc_online_update(xyz, val, xyz.shape[0], nx, ny, nz, cell, minmax)
+    return minmax
+
+
+def mc_mu(minmax, lut):
+    mu = np.zeros(minmax.shape[:-1], dtype=np.float32)
+    lib().or_mc_mu(_f32(minmax), mu.size, _f32(lut), mu)
+    return mu
 
 
 def _cam(cam: dict) -> _Cam:

@@ -373,6 +373,47 @@ def test_macrocells_brute_force():
 
 # -------------------------------------------------------------- renderer ----
 
+def test_online_macrocells_brute_force():
+    # ranges grown from samples equal a per-cell min / max computed by grouping
+    # the samples with numpy, the cell taken from the sample position
+    rng = np.random.default_rng(4)
+    shape, cell = (40, 33, 50), 8
+    x = rng.random((5000, 3), dtype=np.float32)
+    x[:7] = [[0, 0, 0], [1, 1, 1], [0.9999999, 0.5, 0.25], [0.16, 0.16, 0.16], [0.5, 0.5, 0.5],
+             [0.0, 0.999, 0.0], [0.3, 0.2, 0.1]]
+    v = rng.random(5000, dtype=np.float32)
+    mm = O.mc_online_update(O.mc_online_empty(shape, cell), x, v, shape, cell)
+    nc = [-(-n // cell) for n in shape[::-1]]  # x, y, z
+    idx = np.stack([np.clip(np.floor(x[:, a] * np.float32(shape[2 - a] / cell)).astype(int), 0, nc[a] - 1)
+                    for a in range(3)], 1)
+    lo = np.full(nc[::-1], np.inf, np.float32)
+    hi = np.full(nc[::-1], -np.inf, np.float32)
+    np.minimum.at(lo, (idx[:, 2], idx[:, 1], idx[:, 0]), v)
+    np.maximum.at(hi, (idx[:, 2], idx[:, 1], idx[:, 0]), v)
+    np.testing.assert_array_equal(mm[..., 0], lo)
+    np.testing.assert_array_equal(mm[..., 1], hi)
+
+
+def test_online_macrocell_mu_agrees_with_voxel_ranges_and_bounds_them():
+    vol = I.blob_volume((32, 40, 48), seed=6)
+    lut = I.ramp_lut(alpha_floor=0.1)
+    mm_v, mu_v = O.macrocells(vol, 8, lut)
+    # mu from the voxel ranges reproduces the voxel-pass mu exactly
+    np.testing.assert_array_equal(O.mc_mu(mm_v, lut), mu_v)
+    # samples of the volume: their values lie inside the aproned voxel range of
+    # the cell that holds them, so the online mu never exceeds the voxel-pass mu
+    x = O.sample_points(3, 0, 0, 20000)
+    t = O.trilinear(vol, x).astype(np.float32)
+    mm = O.mc_online_update(O.mc_online_empty(vol.shape, 8), x, t, vol.shape, 8)
+    filled = np.isfinite(mm[..., 0])
+    assert filled.mean() > 0.99
+    assert np.all(mm[..., 0][filled] >= mm_v[..., 0][filled])
+    assert np.all(mm[..., 1][filled] <= mm_v[..., 1][filled])
+    mu = O.mc_mu(mm, lut)
+    assert np.all(mu <= mu_v)
+    assert np.all(mu[~filled] == 0)
+
+
 def test_ortho_rays_through_pixel_centres():
     cam = I.ortho_camera_z(64, 64)
     for px, py in [(0, 0), (17, 40), (63, 63)]:
