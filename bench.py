@@ -513,19 +513,34 @@ def extra_cfg4_inloop(nv, I, CF, torch, frames=None):
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     psnr_curve = []
+    # online macrocells (Sec. 5.3): the training samples grow the value ranges,
+    # mu_max is refreshed from them before each frame's render
+    cell = cfg["cell"]
+    mm_on = nv.online_macrocells(vt.shape, cell)
+    mu_on = torch.zeros_like(mu)
+    net.set_online_macrocells(mm_on, vt.shape, cell)
+    mc_on = (mu_on, cell, vt.shape)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for f in range(frames):
         net.train_step(n=cfg["batch"], vol=vt, seed=21, loss_out=loss)
-        r.render(cam, lut, opts, net=net, mc=mc, out=img)
+        nv.macrocells_mu(mm_on, vt.shape, cell, lut, out=mu_on)
+        r.render(cam, lut, opts, net=net, mc=mc_on, out=img)
         if f % 100 == 99:
             psnr_curve.append((f + 1, nv.image_mse(img, raw)))
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / frames
     curve = [(f, _psnr(m.item())) for f, m in psnr_curve]
+    # the last network rendered with ranges precomputed from the voxels instead
+    img_pre = r.render(cam, lut, opts, net=net, mc=mc)
+    psnr_pre = _psnr(nv.image_mse(img_pre, raw).item())
+    cells_on = int((mu_on > 0).sum().item())
+    cells_pre = int((mu > 0).sum().item())
     out = {"frames": frames, "ms_per_frame": ms, "raw_ms": raw_ms, "psnr_db_by_frame": curve,
-           "final_psnr_db": curve[-1][1] if curve else None, "n_params": net.n_params}
+           "final_psnr_db": curve[-1][1] if curve else None, "n_params": net.n_params,
+           "macrocells": "online (training samples)", "final_psnr_db_precomputed_macrocells": psnr_pre,
+           "nonempty_cells_online": cells_on, "nonempty_cells_precomputed": cells_pre}
     net.close()
     r.close()
     del vt

@@ -224,6 +224,26 @@ nv_status nv_ooc_stats(nv_ooc *ooc, int64_t *bytes_copied, double *copy_ms);
 nv_status nv_macrocells_build(const nv_volume *vol, int cell, const float *lut_dev,
                               float *minmax_dev, float *mu_max_dev, void *stream);
 
+/* Online macrocells (Sec. 5.3): instead of a pass over the voxels, the value
+ * ranges grow from the training samples, so the renderer needs no
+ * precomputation over raw data.  minmax_dev [nc][2] (nc = the grid of `cell`
+ * voxels over nx*ny*nz, x fastest) as nv_macrocells_build; a sample at unit
+ * position x widens the range of the cell floor(fl32(x * fl32(n / cell))) per
+ * axis, clamped -- the cell the ray march looks up at that position.
+ * reset: every range empty (+inf, -inf).  update: n samples xyz_dev [n][3]
+ * with values val_dev [n] (NaN values are ignored).  mu: mu_max_dev [nc] as
+ * nv_macrocells_build from the ranges (an empty range gives 0, so cells no
+ * sample reached are skipped).  All asynchronous on `stream`. */
+nv_status nv_macrocells_reset(float *minmax_dev, int nx, int ny, int nz, int cell, void *stream);
+nv_status nv_macrocells_update(const float *xyz_dev, const float *val_dev, int64_t n, int nx, int ny, int nz,
+                               int cell, float *minmax_dev, void *stream);
+nv_status nv_macrocells_mu(const float *minmax_dev, int nx, int ny, int nz, int cell, const float *lut_dev,
+                           float *mu_max_dev, void *stream);
+/* Register minmax_dev (NULL = off) so that every later nv_train_step widens it
+ * with its batch (given or sampled) on the context stream.  The caller owns
+ * the array and keeps it alive while it is registered. */
+nv_status nv_set_online_macrocells(nv_ctx *ctx, float *minmax_dev, int nx, int ny, int nz, int cell);
+
 /* A renderer owns the structure-of-arrays ray state for images of up to
  * max_pixels pixels and K samples per ray per iteration. */
 nv_status nv_renderer_create(int64_t max_pixels, int K, void *cuda_stream, nv_renderer **out);

@@ -35,6 +35,17 @@ __global__ void k_sample(nv_volume v, int64_t n, uint64_t seed, uint32_t step, f
   if (t) t[i] = nv_trilinear(v.data_dev, v.nx, v.ny, v.nz, p.x, p.y, p.z);
 }
 
+// Largest LUT opacity over the entries floor(255 lo) .. ceil(255 hi) of a value
+// range clamped to [0, 1] (FP32 products decide the indices); an empty range
+// (lo = +inf, hi = -inf) covers no entry and gives 0.
+__device__ __forceinline__ float mu_of_range(float lo, float hi, const float *__restrict__ lut) {
+  const float a0 = fminf(fmaxf(lo, 0.f), 1.f), a1 = fminf(fmaxf(hi, 0.f), 1.f);
+  const int e0 = (int)floorf(__fmul_rn(a0, 255.0f)), e1 = min((int)ceilf(__fmul_rn(a1, 255.0f)), 255);
+  float m = 0.f;
+  for (int e = e0; e <= e1; ++e) m = fmaxf(m, lut[4 * e + 3]);
+  return m;
+}
+
 // One CTA per macrocell: min/max over the aproned voxel range, then mu_max
 // from the transfer function over the covered LUT entries.
 __global__ void __launch_bounds__(256) k_macrocells(nv_volume v, int cell, int ncx, int ncy,
@@ -73,13 +84,69 @@ __global__ void __launch_bounds__(256) k_macrocells(nv_volume v, int cell, int n
       minmax[2 * c] = lo;
       minmax[2 * c + 1] = hi;
     }
-    if (mu) {
-      float a0 = fminf(fmaxf(lo, 0.f), 1.f), a1 = fminf(fmaxf(hi, 0.f), 1.f);
-      int e0 = (int)floorf(__fmul_rn(a0, 255.0f)), e1 = min((int)ceilf(__fmul_rn(a1, 255.0f)), 255);
-      float m = 0.f;
-      for (int e = e0; e <= e1; ++e) m = fmaxf(m, lut[4 * e + 3]);
-      mu[c] = m;
-    }
+    if (mu) mu[c] = mu_of_range(lo, hi, lut);
+  }
+}
+
+// Online macrocells (Sec. 5.3): training samples widen the value range of the
+// macrocell that holds them (the cell of the position, as the march looks it
+// up), with float atomic min / max.
+struct McGrid {
+  int ncx, ncy, ncz;
+  float sx, sy, sz;  // cells per unit length (n / cell, FP32)
+};
+
+__device__ __forceinline__ void atomic_min_f(float *a, float v) {
+  if (v >= 0.f) atomicMin(reinterpret_cast<int *>(a), __float_as_int(v));
+  else atomicMax(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_f(float *a, float v) {
+  if (v >= 0.f) atomicMax(reinterpret_cast<int *>(a), __float_as_int(v));
+  else atomicMin(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+
+__device__ __forceinline__ void mc_widen(float *minmax, const McGrid &g, float x, float y, float z, float v) {
+  if (v != v) return;  // NaN widens nothing
+  v += 0.0f;           // -0 -> +0, so the integer orderings above hold
+  const int cx = min(max((int)floorf(__fmul_rn(x, g.sx)), 0), g.ncx - 1);
+  const int cy = min(max((int)floorf(__fmul_rn(y, g.sy)), 0), g.ncy - 1);
+  const int cz = min(max((int)floorf(__fmul_rn(z, g.sz)), 0), g.ncz - 1);
+  float *m = minmax + 2 * (((int64_t)cz * g.ncy + cy) * g.ncx + cx);
+  if (v < m[0]) atomic_min_f(m, v);
+  if (v > m[1]) atomic_max_f(m + 1, v);
+}
+
+__global__ void k_mc_reset(float2 *minmax, int64_t nc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nc) minmax[i] = make_float2(__int_as_float(0x7f800000), __int_as_float(0xff800000));
+}
+
+// xyz (nullable: Philox training sample of (seed, step), target from vol) and val
+__global__ void k_mc_update(const float *__restrict__ xyz, const float *__restrict__ val, int64_t n, nv_volume vol,
+                            uint64_t seed, uint32_t step, McGrid g, float *minmax) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x, y, z, v;
+  if (xyz) {
+    x = xyz[3 * i];
+    y = xyz[3 * i + 1];
+    z = xyz[3 * i + 2];
+    v = val[i];
+  } else {
+    const float3 p = nv_sample_point(seed, step, (uint64_t)i);
+    x = p.x;
+    y = p.y;
+    z = p.z;
+    v = nv_trilinear(vol.data_dev, vol.nx, vol.ny, vol.nz, x, y, z);
+  }
+  mc_widen(minmax, g, x, y, z, v);
+}
+
+__global__ void k_mc_mu(const float2 *__restrict__ minmax, int64_t nc, const float *__restrict__ lut, float *mu) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nc) {
+    const float2 r = minmax[i];
+    mu[i] = mu_of_range(r.x, r.y, lut);
   }
 }
 
@@ -256,6 +323,33 @@ nv_status launch_macrocells(const nv_volume &v, int cell, const float *lut, floa
   int64_t nc = (int64_t)ncx * ncy * ncz;
   k_macrocells<<<(unsigned)nc, 256, 0, s>>>(v, cell, ncx, ncy, lut, minmax, mu);
   return nv_cuda_check(cudaGetLastError(), "k_macrocells launch");
+}
+
+static McGrid mc_grid(int nx, int ny, int nz, int cell) {
+  return McGrid{(nx + cell - 1) / cell, (ny + cell - 1) / cell, (nz + cell - 1) / cell,
+                (float)nx / (float)cell, (float)ny / (float)cell, (float)nz / (float)cell};
+}
+
+nv_status launch_mc_reset(float *minmax, int nx, int ny, int nz, int cell, cudaStream_t s) {
+  const McGrid g = mc_grid(nx, ny, nz, cell);
+  const int64_t nc = (int64_t)g.ncx * g.ncy * g.ncz;
+  k_mc_reset<<<blocks_for(nc, 256), 256, 0, s>>>(reinterpret_cast<float2 *>(minmax), nc);
+  return nv_cuda_check(cudaGetLastError(), "k_mc_reset launch");
+}
+
+nv_status launch_mc_update(const float *xyz, const float *val, int64_t n, const nv_volume &vol, uint64_t seed,
+                           uint32_t step, int nx, int ny, int nz, int cell, float *minmax, cudaStream_t s) {
+  if (n == 0) return NV_OK;
+  k_mc_update<<<blocks_for(n, 256), 256, 0, s>>>(xyz, val, n, vol, seed, step, mc_grid(nx, ny, nz, cell), minmax);
+  return nv_cuda_check(cudaGetLastError(), "k_mc_update launch");
+}
+
+nv_status launch_mc_mu(const float *minmax, int nx, int ny, int nz, int cell, const float *lut, float *mu,
+                       cudaStream_t s) {
+  const McGrid g = mc_grid(nx, ny, nz, cell);
+  const int64_t nc = (int64_t)g.ncx * g.ncy * g.ncz;
+  k_mc_mu<<<blocks_for(nc, 256), 256, 0, s>>>(reinterpret_cast<const float2 *>(minmax), nc, lut, mu);
+  return nv_cuda_check(cudaGetLastError(), "k_mc_mu launch");
 }
 
 nv_status launch_image_mse(const float *a, const float *b, int64_t n, double *out, cudaStream_t s) {

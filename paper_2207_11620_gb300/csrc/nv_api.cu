@@ -378,12 +378,54 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
   } else {
     NV_TRY(launch_mlp_tc(c, MODE_TRAIN, a));  // times its encode and MLP kernels itself
   }
+  if (c->mc_minmax) {  // online macrocells (Sec. 5.3): this step's samples widen the ranges
+    int tk1 = prof_begin(c);
+    NV_TRY(launch_mc_update(a.xyz, a.in, n, a.vol, a.seed, a.sample_step, c->mc_nx, c->mc_ny, c->mc_nz,
+                            c->mc_cell, c->mc_minmax, c->stream));
+    prof_end(c, NV_K_OTHER, tk1);
+  }
   int tk = prof_begin(c);
   NV_TRY(launch_adam(c));
   prof_end(c, NV_K_ADAM, tk);
   tk = prof_begin(c);
   NV_TRY(launch_step_finish(c, 1.0 / (double)n, loss_dev));
   prof_end(c, NV_K_FINISH, tk);
+  return NV_OK;
+}
+
+static nv_status check_mc_grid(int nx, int ny, int nz, int cell, const char *who) {
+  if (nx < 1 || ny < 1 || nz < 1 || cell < 1) return nv_fail(NV_ERR_ARG, "%s: grid %dx%dx%d / cell %d", who, nx, ny, nz, cell);
+  return NV_OK;
+}
+
+extern "C" nv_status nv_macrocells_reset(float *minmax, int nx, int ny, int nz, int cell, void *stream) {
+  if (!minmax) return nv_fail(NV_ERR_ARG, "nv_macrocells_reset: minmax is NULL");
+  NV_TRY(check_mc_grid(nx, ny, nz, cell, "nv_macrocells_reset"));
+  return launch_mc_reset(minmax, nx, ny, nz, cell, (cudaStream_t)stream);
+}
+
+extern "C" nv_status nv_macrocells_update(const float *xyz, const float *val, int64_t n, int nx, int ny, int nz,
+                                          int cell, float *minmax, void *stream) {
+  if (!xyz || !val || !minmax || n < 0) return nv_fail(NV_ERR_ARG, "nv_macrocells_update: bad argument");
+  NV_TRY(check_mc_grid(nx, ny, nz, cell, "nv_macrocells_update"));
+  return launch_mc_update(xyz, val, n, nv_volume{}, 0, 0, nx, ny, nz, cell, minmax, (cudaStream_t)stream);
+}
+
+extern "C" nv_status nv_macrocells_mu(const float *minmax, int nx, int ny, int nz, int cell, const float *lut,
+                                      float *mu, void *stream) {
+  if (!minmax || !lut || !mu) return nv_fail(NV_ERR_ARG, "nv_macrocells_mu: NULL argument");
+  NV_TRY(check_mc_grid(nx, ny, nz, cell, "nv_macrocells_mu"));
+  return launch_mc_mu(minmax, nx, ny, nz, cell, lut, mu, (cudaStream_t)stream);
+}
+
+extern "C" nv_status nv_set_online_macrocells(nv_ctx *c, float *minmax, int nx, int ny, int nz, int cell) {
+  if (!c) return nv_fail(NV_ERR_ARG, "nv_set_online_macrocells: ctx is NULL");
+  if (minmax) NV_TRY(check_mc_grid(nx, ny, nz, cell, "nv_set_online_macrocells"));
+  c->mc_minmax = minmax;
+  c->mc_nx = nx;
+  c->mc_ny = ny;
+  c->mc_nz = nz;
+  c->mc_cell = cell;
   return NV_OK;
 }
 

@@ -48,6 +48,8 @@ struct nv_ctx {
   DevState *ds;
   nv_adam_cfg adam;
   int loss_kind;                            // nv_loss of nv_train_step
+  float *mc_minmax;                         // online macrocell ranges the training samples widen (or NULL)
+  int mc_nx, mc_ny, mc_nz, mc_cell;
   uint32_t sample_counter;                  // Philox step word of sampled batches
   int params_set;
   float *batch;                             // staging for host batches: [cap][3] xyz + [cap] target
@@ -270,6 +272,14 @@ nv_status launch_macrocells(const nv_volume &v, int cell, const float *lut, floa
                             float *mu, cudaStream_t s);
 nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera &cam,
                       const float *lut, const nv_macrocells *mc, const nv_render_opts &o, float *rgba);
+// Online macrocells (k_render.cu): ranges reset to empty, widened by samples
+// (xyz == NULL: the Philox training sample of (seed, step) with its target from
+// vol), mu_max from the ranges.
+nv_status launch_mc_reset(float *minmax, int nx, int ny, int nz, int cell, cudaStream_t s);
+nv_status launch_mc_update(const float *xyz, const float *val, int64_t n, const nv_volume &vol, uint64_t seed,
+                           uint32_t step, int nx, int ny, int nz, int cell, float *minmax, cudaStream_t s);
+nv_status launch_mc_mu(const float *minmax, int nx, int ny, int nz, int cell, const float *lut, float *mu,
+                       cudaStream_t s);
 // In-shader ray march (k_inshader.cu); samples (nullable, device) counts the
 // evaluated samples.
 nv_status render_inshader(nv_ctx *c, const nv_camera &cam, const float *lut, const nv_macrocells *mc,

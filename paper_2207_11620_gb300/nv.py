@@ -65,6 +65,12 @@ EXPORTS = {
     "nv_set_adam": ([C.c_void_p, C.POINTER(AdamCfg)], C.c_int),
     "nv_set_loss_scale": ([C.c_void_p, C.c_float], C.c_int),
     "nv_set_loss": ([C.c_void_p, C.c_int], C.c_int),
+    "nv_macrocells_reset": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p], C.c_int),
+    "nv_macrocells_update": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                              C.c_void_p], C.c_int),
+    "nv_macrocells_mu": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
+                         C.c_int),
+    "nv_set_online_macrocells": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "nv_render_inshader": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
                            C.c_int),
     "nv_get_step": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float)], C.c_int),
@@ -245,6 +251,18 @@ class NeuralVolume:
         cfg = AdamCfg(lr, beta1, beta2, eps, l2_reg, decay_start, decay_interval, decay_base)
         _check(lib().nv_set_adam(self._h, C.byref(cfg)))
 
+    def set_online_macrocells(self, minmax, shape=None, cell=None):
+        """Let every later train_step widen `minmax` (from online_macrocells) with its
+        batch; None turns it off.  shape = volume (nz, ny, nx)."""
+        if minmax is None:
+            _check(lib().nv_set_online_macrocells(self._h, None, 0, 0, 0, 0))
+            self._mc = None
+            return
+        nz, ny, nx = shape
+        _check(lib().nv_set_online_macrocells(self._h, _dev(minmax, name="minmax"), int(nx), int(ny), int(nz),
+                                              int(cell)))
+        self._mc = minmax  # keep it alive while registered
+
     def set_loss(self, loss):
         """'l2' (default) or 'l1'."""
         _check(lib().nv_set_loss(self._h, {"l2": 0, "l1": 1}[loss]))
@@ -384,6 +402,31 @@ class Renderer:
         it, sm = C.c_int(), C.c_int64()
         _check(lib().nv_render_stats(self._h, C.byref(it), C.byref(sm)))
         return it.value, sm.value
+
+
+def online_macrocells(shape, cell):
+    """Empty online macrocell ranges [ncz, ncy, ncx, 2] for a volume of shape (nz, ny, nx)."""
+    nc = tuple(-(-int(n) // cell) for n in shape)
+    mm = torch.empty(nc + (2,), dtype=torch.float32, device="cuda")
+    nz, ny, nx = shape
+    _check(lib().nv_macrocells_reset(_dev(mm, name="minmax"), int(nx), int(ny), int(nz), int(cell), _stream()))
+    return mm
+
+
+def macrocells_update(minmax, xyz, val, shape, cell):
+    nz, ny, nx = shape
+    _check(lib().nv_macrocells_update(_dev(xyz, name="xyz"), _dev(val, name="val"), xyz.shape[0], int(nx),
+                                      int(ny), int(nz), int(cell), _dev(minmax, name="minmax"), _stream()))
+    return minmax
+
+
+def macrocells_mu(minmax, shape, cell, lut, out=None):
+    nz, ny, nx = shape
+    if out is None:
+        out = torch.empty(minmax.shape[:-1], dtype=torch.float32, device="cuda")
+    _check(lib().nv_macrocells_mu(_dev(minmax, name="minmax"), int(nx), int(ny), int(nz), int(cell),
+                                  _dev(lut, name="lut"), _dev(out, name="mu"), _stream()))
+    return out
 
 
 def render_inshader(net: NeuralVolume, cam: dict, lut, opts: dict, mc: tuple | None = None, out=None,
