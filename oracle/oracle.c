@@ -505,7 +505,66 @@ typedef struct {
   float alpha_exp; /* opacity-correction exponent: step / s1 */
   float et;        /* early-termination opacity */
   int mc_cell;     /* macrocell size in voxels (0: no empty-space skipping) */
+  float step_max;  /* > 0: adaptive step (Sec. 5.3) between step and step_max; needs macrocells */
 } or_opts;
+
+/* One step of the adaptive ray march (Sec. 5.3, Eq. 3) in FP32, every
+ * operation rounded on its own.  From the ray parameter *t, in the macrocell
+ * c holding o + (t + s1 / 1024) d: the segment runs to the nearest of the
+ * cell's exit, t1 and t + s_bar, s_bar = max(s1 + (s2 - s1) (1 - min(mu_c,
+ * 1))^2, s1) with p = 2 (readings: the step is taken from the cell the segment
+ * starts in -- looked up just past the start, so a ray standing on a face
+ * moves on into the next cell -- a segment never crosses a cell face, the
+ * sample sits at its midpoint, and a segment is at least s1 / 1024 long).  A
+ * cell with mu_c = 0 is
+ * crossed without a sample.  Returns 0 at the end of the ray (t >= t1), 2 for
+ * a crossed transparent cell, 1 for a sample at pos whose opacity exponent is
+ * *e = alpha_exp * seg / s1; *t moves to the end of the segment. */
+int or_march_adaptive_step(const float *o, const float *d, float t1, float s1, float s2, float alpha_exp,
+                           const float *mumax, int ncx, int ncy, int ncz, float sx, float sy, float sz,
+                           float *t, float *pos, float *e) {
+  if (!(*t < t1)) return 0;
+  float tiny = s1 * 0.0009765625f;
+  float tc = *t + tiny;
+  float p[3];
+  for (int a = 0; a < 3; ++a) { float m = tc * d[a]; p[a] = o[a] + m; }
+  int nc[3] = {ncx, ncy, ncz};
+  float sc[3] = {sx, sy, sz};
+  int c[3];
+  for (int a = 0; a < 3; ++a) {
+    c[a] = (int)floorf(p[a] * sc[a]);
+    if (c[a] < 0) c[a] = 0;
+    if (c[a] > nc[a] - 1) c[a] = nc[a] - 1;
+  }
+  float texit = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    float face;
+    if (d[a] > 0.f) face = (float)(c[a] + 1) / sc[a];
+    else if (d[a] < 0.f) face = (float)c[a] / sc[a];
+    else continue;
+    float num = face - o[a];
+    float ta = num / d[a];
+    texit = fminf(texit, ta);
+  }
+  texit = fminf(texit, t1);
+  float room = texit - *t;
+  if (!(room > tiny)) room = tiny;
+  float mu = mumax[((int64_t)c[2] * ncy + c[1]) * ncx + c[0]];
+  if (mu == 0.0f) { *t = *t + room; return 2; }
+  float q = 1.0f - fminf(mu, 1.0f);
+  float q2 = q * q;
+  float ds = s2 - s1;
+  float grow = ds * q2;
+  float sbar = fmaxf(s1 + grow, s1);
+  float seg = fminf(sbar, room);
+  float half = 0.5f * seg;
+  float tm = *t + half;
+  for (int a = 0; a < 3; ++a) { float m = tm * d[a]; pos[a] = o[a] + m; }
+  float ratio = seg / s1;
+  *e = alpha_exp * ratio;
+  *t = *t + seg;
+  return 1;
+}
 
 /* A-11: the ray through the centre of pixel (px, py), FP32 operation by
  * operation (it decides the sample positions).  forward = normalize(target -
@@ -623,7 +682,30 @@ void or_render_pixels(const or_camera *cam, const float *lut, const or_opts *opt
       float o[3], d[3], t0, t1;
       double C[3] = {0, 0, 0}, A = 0.0;
       or_ray(cam, px, py, o, d);
-      if (or_box(o, d, &t0, &t1)) {
+      if (or_box(o, d, &t0, &t1) && opt->step_max > 0.0f) {
+        /* adaptive step (Sec. 5.3): segments from or_march_adaptive_step */
+        float t = t0;
+        for (;;) {
+          float pos[3], e;
+          int r = or_march_adaptive_step(o, d, t1, opt->step, opt->step_max, opt->alpha_exp, mumax, ncx, ncy,
+                                         ncz, sx, sy, sz, &t, pos, &e);
+          if (r == 0) break;
+          if (r == 2) continue;
+          double val;
+          if (use_net) {
+            or_encode_point(L, F, log2T, res, params, pos, act);
+            val = or_mlp_point(dims, n_dims, weights, act);
+          } else {
+            val = or_trilinear_point(vol, nx, ny, nz, pos);
+          }
+          double c[4];
+          or_tf(lut, val, c);
+          double a = 1.0 - pow(1.0 - c[3], (double)e);
+          for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * a * c[ch];
+          A += (1.0 - A) * a;
+          if (A >= (double)opt->et) break;
+        }
+      } else if (or_box(o, d, &t0, &t1)) {
         for (int64_t k = 0;; ++k) {
           float tk = ((float)k + 0.5f) * opt->step;
           tk = t0 + tk;

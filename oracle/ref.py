@@ -45,7 +45,7 @@ class _Cam(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("step", C.c_float), ("alpha_exp", C.c_float), ("et", C.c_float),
-                ("mc_cell", C.c_int)]
+                ("mc_cell", C.c_int), ("step_max", C.c_float)]
 
 
 _lib = None
@@ -90,6 +90,10 @@ def lib():
         L.or_macrocells.argtypes = [_f32p, C.c_int, C.c_int, C.c_int, C.c_int, _f32p, _f32p, _f32p]
         L.or_mc_online_update.argtypes = [_f32p, _f32p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _f32p]
         L.or_mc_mu.argtypes = [_f32p, C.c_int64, _f32p, _f32p]
+        L.or_march_adaptive_step.argtypes = [_f32p, _f32p, C.c_float, C.c_float, C.c_float, C.c_float, _f32p,
+                                             C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
+                                             C.POINTER(C.c_float), _f32p, C.POINTER(C.c_float)]
+        L.or_march_adaptive_step.restype = C.c_int
         L.or_render_pixels.argtypes = [C.POINTER(_Cam), _f32p, C.POINTER(_Opts), C.c_int, C.c_int,
                                        C.c_int, C.c_int, _i32p, _i32p, C.c_int, C.c_void_p,
                                        C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, _i64p,
@@ -289,6 +293,33 @@ def macrocells(vol, cell, lut):
     return mm, mu
 
 
+def march_adaptive(cam: dict, px, py, opts: dict, mumax, shape):
+    """The adaptive march of one pixel as a list of (kind, t_before, t_after, pos, e):
+    kind 1 = sample, 2 = crossed transparent cell."""
+    o = np.zeros(3, np.float32)
+    d = np.zeros(3, np.float32)
+    t01 = np.zeros(2, np.float32)
+    if not lib().or_pixel_ray(C.byref(_cam(cam)), int(px), int(py), o, d, t01):
+        return []
+    cell = int(opts["mc_cell"])
+    nz, ny, nx = shape
+    nc = [-(-n // cell) for n in (nx, ny, nz)]
+    sc = [np.float32(n) / np.float32(cell) for n in (nx, ny, nz)]
+    mu = _f32(mumax)
+    t = C.c_float(t01[0])
+    e = C.c_float(0.0)
+    pos = np.zeros(3, np.float32)
+    steps = []
+    while True:
+        tb = t.value
+        r = lib().or_march_adaptive_step(o, d, float(t01[1]), float(opts["step"]), float(opts["step_max"]),
+                                         float(opts.get("alpha_exp", 1.0)), mu, nc[0], nc[1], nc[2],
+                                         float(sc[0]), float(sc[1]), float(sc[2]), C.byref(t), pos, C.byref(e))
+        if r == 0:
+            return steps
+        steps.append((r, np.float32(tb), np.float32(t.value), pos.copy(), np.float32(e.value)))
+
+
 def mc_online_empty(shape, cell):
     """Empty online value ranges [ncz, ncy, ncx, 2] (+inf, -inf) for a volume of `shape` (nz, ny, nx)."""
     nc = tuple(-(-n // cell) for n in shape)
@@ -343,6 +374,9 @@ def render_pixels(cam: dict, lut, opts: dict, pixels, net: Net | None = None, pa
     o.alpha_exp = float(opts.get("alpha_exp", 1.0))
     o.et = float(opts.get("et", 0.99))
     o.mc_cell = int(opts.get("mc_cell", 0))
+    o.step_max = float(opts.get("step_max", 0.0))
+    if o.step_max > 0 and o.mc_cell <= 0:
+        raise ValueError("the adaptive step needs macrocells (mc_cell > 0)")
     pix = np.ascontiguousarray(pixels, dtype=np.int64)
     out = np.zeros((pix.shape[0], 4), dtype=np.float64)
     if vol is not None:

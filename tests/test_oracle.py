@@ -414,6 +414,108 @@ def test_online_macrocell_mu_agrees_with_voxel_ranges_and_bounds_them():
     assert np.all(mu[~filled] == 0)
 
 
+@pytest.mark.parametrize("cell", [4, 16])
+@pytest.mark.parametrize("smax_factor", [1.0, 8.0, 64.0])
+@pytest.mark.parametrize("persp", [False, True])
+def test_adaptive_step_beer_lambert(cell, smax_factor, persp):
+    # constant medium: whatever segments the adaptive march cuts, the opacity
+    # exponents add up to the path length, A = 1 - (1 - a)^(L / s_ref) and the
+    # colour is rgb * A
+    n = 32
+    v = np.float32(100.0 / 255.0)
+    vol = np.full((n, n, n), v, np.float32)
+    lut = I.ramp_lut()
+    _, mu = O.macrocells(vol, cell, lut)
+    s1 = np.float32(0.5 / n)
+    opts = dict(step=float(s1), alpha_exp=0.5, et=2.0, mc_cell=cell, step_max=float(s1 * smax_factor))
+    cam = I.perspective_camera(9, 7) if persp else I.ortho_camera_z(9, 7)
+    pix = np.arange(63)
+    got = O.render_pixels(cam, lut, opts, pix, vol=vol, mumax=mu)
+    a = float(lut[100, 3])
+    for q, p in enumerate(pix):
+        hit, o, d, t01 = O.pixel_ray(cam, p % 9, p // 9)
+        if not hit:
+            assert np.all(got[q] == 0)
+            continue
+        L = float(t01[1]) - float(t01[0])
+        A = 1.0 - (1.0 - a) ** (L * n)  # s_ref = one voxel = 1 / n
+        assert got[q, 3] == pytest.approx(A, abs=2e-5), (q, got[q, 3], A)
+        assert got[q, 0] == pytest.approx(float(lut[100, 0]) * got[q, 3], rel=1e-5)
+
+
+def test_adaptive_step_segments_tile_the_ray():
+    # brute-force invariants of the segment sequence on a random macrocell grid
+    # with transparent cells: contiguous, never across a face, s_bar where the
+    # cell and t1 leave room, samples only in non-empty cells
+    rng = np.random.default_rng(3)
+    shape, cell = (40, 36, 44), 4
+    nc = [-(-n // cell) for n in shape]
+    mu = rng.random(nc).astype(np.float32)
+    mu[rng.random(nc) < 0.4] = 0.0
+    s1 = np.float32(0.5 / 44)
+    s2 = np.float32(16 * s1)
+    opts = dict(step=float(s1), step_max=float(s2), alpha_exp=0.5, mc_cell=cell)
+    cam = I.perspective_camera(24, 20, eye=(0.31, 0.62, -0.9))
+    sc = [np.float32(n) / np.float32(cell) for n in shape[::-1]]  # x, y, z
+
+    def cell_of(pt):
+        return tuple(int(np.clip(np.floor(np.float32(pt[a]) * sc[a]), 0, nc[2 - a] - 1)) for a in range(3))
+
+    n_samples = n_short = n_tiny = 0
+    for p in rng.choice(24 * 20, 60, replace=False):
+        hit, o, d, t01 = O.pixel_ray(cam, p % 24, p // 24)
+        steps = O.march_adaptive(cam, p % 24, p // 24, opts, mu, shape)
+        if not hit:
+            assert steps == []
+            continue
+        t = np.float32(t01[0])
+        for kind, tb, ta, pos, e in steps:
+            assert tb == t and ta > tb
+            t = ta
+            tiny = s1 * np.float32(0.0009765625)
+            start = o + np.float32(tb + tiny) * d
+            c = cell_of(start)
+            m = mu[c[2], c[1], c[0]]
+            seg = np.float32(ta - tb)
+            if kind == 2:
+                assert m == 0
+                continue
+            n_samples += 1
+            assert m > 0
+            q = np.float32(1) - min(m, np.float32(1))
+            sbar = max(s1 + (s2 - s1) * q * q, s1)
+            assert seg <= sbar + 4 * np.spacing(np.float32(ta))  # seg re-derived from rounded t
+            n_tiny += seg <= tiny * np.float32(1.0001)
+            if seg > 2 * tiny:
+                assert cell_of(pos) == c  # the midpoint stays in the start cell
+            assert abs(e - 0.5 * seg / s1) <= 0.5 * 4 * np.spacing(np.float32(ta)) / s1 + 1e-6 * e
+            if seg < sbar * (1 - 1e-5) and ta < t01[1] * (1 - 1e-6):
+                n_short += 1  # cut by the face: just past the end is another cell
+                assert cell_of(o + np.float32(ta + 1e-4 * s1) * d) != c or seg <= s1 / 1024 * 1.01
+        assert t >= t01[1]
+    assert n_samples > 500 and n_short > 50
+    assert n_tiny <= 0.01 * n_samples  # slivers only where a ray clips a cell corner
+
+
+def test_adaptive_step_without_adaptivity_is_the_midpoint_rule():
+    # s2 = s1 and one macrocell over the whole volume: every segment but the
+    # last is s1 long, so the samples sit at t0 + (k + 1/2) s1
+    shape, cell = (16, 16, 16), 16
+    mu = np.ones((1, 1, 1), np.float32)
+    s1 = np.float32(1.0 / 64)
+    opts = dict(step=float(s1), step_max=float(s1), alpha_exp=1.0, mc_cell=cell)
+    cam = I.perspective_camera(5, 5)
+    for p in range(25):
+        hit, o, d, t01 = O.pixel_ray(cam, p % 5, p // 5)
+        steps = O.march_adaptive(cam, p % 5, p // 5, opts, mu, shape)
+        if not hit:
+            continue
+        for k, (kind, tb, ta, pos, e) in enumerate(steps[:-1]):
+            tk = np.float64(t01[0]) + (k + 0.5) * np.float64(s1)
+            np.testing.assert_allclose(pos, o + tk * d, atol=2e-6)
+            assert e == pytest.approx(1.0, rel=1e-5)
+
+
 def test_ortho_rays_through_pixel_centres():
     cam = I.ortho_camera_z(64, 64)
     for px, py in [(0, 0), (17, 40), (63, 63)]:
