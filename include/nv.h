@@ -83,6 +83,8 @@ typedef struct {
   float alpha_exp; /* opacity correction exponent step / s1 (Sec. 5.3): a' = 1 - (1 - a)^e */
   float et;        /* early termination once accumulated opacity >= et (e.g. 0.99) */
   int K;           /* samples streamed per live ray per iteration (Sec. 5.2.1; ~8) */
+  float step_max;  /* > 0: adaptive step (Sec. 5.3, Eq. 3) between `step` (s1) and step_max (s2), p = 2;
+                      needs macrocells; 0: fixed step */
 } nv_render_opts;
 
 typedef struct {
@@ -256,7 +258,12 @@ nv_status nv_renderer_destroy(nv_renderer *r);
  * inference) or, when net is NULL, from the raw volume `raw` by trilinear
  * interpolation -- then front-to-back compositing with opacity correction
  * and early termination, and compaction of the live rays.  mc may be NULL (no
- * skipping).  rgba_dev [height][width][4]; rays that miss are black. */
+ * skipping).  rgba_dev [height][width][4]; rays that miss are black.
+ * opts->step_max > 0 selects the adaptive step (Sec. 5.3, Eq. 3; needs mc):
+ * each segment takes s_bar = max(s1 + (s2 - s1) (1 - min(mu, 1))^2, s1) from
+ * the macrocell it starts in, ends at that cell's face, t1 or s_bar, samples
+ * its midpoint and corrects the opacity by its own length; transparent cells
+ * are crossed without samples. */
 nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
                     const float *lut_dev, const nv_macrocells *mc, const nv_render_opts *opts,
                     float *rgba_dev);

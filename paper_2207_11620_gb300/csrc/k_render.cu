@@ -162,7 +162,9 @@ __device__ __forceinline__ int warp_append(int *counter, bool pred) {
   return base + __popc(mask & ((1u << lane) - 1u));
 }
 
-__global__ void k_raygen(nv_camera cam, float *ray, int *next_k, int64_t cap, int *count, float4 *rgba) {
+// next_k starts at sample 0, or, for the adaptive step, at the ray parameter t0 (float bits).
+__global__ void k_raygen(nv_camera cam, float *ray, int *next_k, int64_t cap, int *count, float4 *rgba,
+                         bool adaptive) {
   const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t npix = (int64_t)cam.width * cam.height;
   bool hit = false;
@@ -187,13 +189,16 @@ __global__ void k_raygen(nv_camera cam, float *ray, int *next_k, int64_t cap, in
     ray[R_CB * cap + slot] = 0.f;
     ray[R_CA * cap + slot] = 0.f;
     ray[R_PIX * cap + slot] = __int_as_float((int)pix);
-    next_k[slot] = 0;
+    next_k[slot] = adaptive ? __float_as_int(t0) : 0;
   }
 }
 
 // Next K sample positions of each live ray (A-12, march_step).
+// seg_exp (non-NULL: adaptive step between step and step_max): the opacity
+// exponent of each emitted sample; next_k then holds the ray parameter t.
 __global__ void k_coords(const float *__restrict__ ray, int *next_k, int64_t cap, const int *count, int K,
-                         float step, McView mc, float *coords, int *nvalid) {
+                         float step, float step_max, float alpha_exp, McView mc, float *coords, float *seg_exp,
+                         int *nvalid) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *count) return;
   const float o[3] = {ray[R_OX * cap + i], ray[R_OY * cap + i], ray[R_OZ * cap + i]};
@@ -202,16 +207,33 @@ __global__ void k_coords(const float *__restrict__ ray, int *next_k, int64_t cap
   int k = next_k[i];
   int cnt = 0;
   float pos[3];
-  while (cnt < K) {
-    const int m = march_step(o, d, t0, t1, step, mc, k, pos);
-    if (m == kMarchEnd) break;
-    if (m == kMarchSkip) continue;
-    float *dst = coords + (i * K + cnt) * 3;
-    dst[0] = pos[0];
-    dst[1] = pos[1];
-    dst[2] = pos[2];
-    ++cnt;
-    ++k;
+  if (seg_exp) {
+    float t = __int_as_float(k);
+    while (cnt < K) {
+      float e;
+      const int m = march_step_adaptive(o, d, t1, step, step_max, alpha_exp, mc, t, pos, e);
+      if (m == kMarchEnd) break;
+      if (m == kMarchSkip) continue;
+      float *dst = coords + (i * K + cnt) * 3;
+      dst[0] = pos[0];
+      dst[1] = pos[1];
+      dst[2] = pos[2];
+      seg_exp[i * K + cnt] = e;
+      ++cnt;
+    }
+    k = __float_as_int(t);
+  } else {
+    while (cnt < K) {
+      const int m = march_step(o, d, t0, t1, step, mc, k, pos);
+      if (m == kMarchEnd) break;
+      if (m == kMarchSkip) continue;
+      float *dst = coords + (i * K + cnt) * 3;
+      dst[0] = pos[0];
+      dst[1] = pos[1];
+      dst[2] = pos[2];
+      ++cnt;
+      ++k;
+    }
   }
   for (int j = cnt; j < K; ++j) {
     float *dst = coords + (i * K + j) * 3;
@@ -236,7 +258,8 @@ __global__ void k_values_raw(nv_volume v, const float *__restrict__ coords, cons
 // at A >= et, and compaction of the rays that stay alive.
 __global__ void k_composite(const float *__restrict__ ray, const int *__restrict__ next_k_in, int64_t cap,
                             const int *count, const float *__restrict__ values, const int *__restrict__ nvalid,
-                            int K, const float *__restrict__ lut, float alpha_exp, float et, float *ray_out,
+                            const float *__restrict__ seg_exp, int K, const float *__restrict__ lut,
+                            float alpha_exp, float et, float *ray_out,
                             int *next_k_out, int *count_out, float4 *rgba, unsigned long long *samples) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int n = *count;
@@ -251,7 +274,8 @@ __global__ void k_composite(const float *__restrict__ ray, const int *__restrict
     nv = nvalid[i];
     bool done = false;
     for (int j = 0; j < nv; ++j) {
-      if (composite_one(values[i * K + j], lut, alpha_exp, et, cr, cg, cb, ca)) {
+      const float ex = seg_exp ? seg_exp[i * K + j] : alpha_exp;
+      if (composite_one(values[i * K + j], lut, ex, et, cr, cg, cb, ca)) {
         done = true;
         break;
       }
@@ -372,13 +396,19 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   if (e == cudaSuccess) e = cudaMemsetAsync(r->d_samples, 0, sizeof(int64_t), st);
   if (e != cudaSuccess) return nv_cuda_check(e, "render memset");
   float4 *out = reinterpret_cast<float4 *>(rgba);
-  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r->ray[0], r->next_k[0], cap, &r->counters[0], out);
+  const bool adaptive = o.step_max > 0.f;
+  float *seg_exp = adaptive ? r->seg_exp : nullptr;
+  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r->ray[0], r->next_k[0], cap, &r->counters[0], out,
+                                                  adaptive);
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
 
   const McView mv = mc_view(mc);
-  // every iteration consumes at least one sample of each live ray, or ends it
-  const int64_t max_iter = (int64_t)std::ceil(1.7320509 / (double)o.step / (double)K) + 4;
+  // every iteration consumes at least one sample of each live ray, or ends it;
+  // adaptive segments also end at every cell face a ray crosses
+  int64_t max_samples = (int64_t)std::ceil(1.7320509 / (double)o.step);
+  if (adaptive) max_samples = max_samples * 1025 / 1024 + 3 * (int64_t)(mv.ncx + mv.ncy + mv.ncz) + 8;
+  const int64_t max_iter = (max_samples + K - 1) / K + 4;
   const int R = 4;  // iterations in flight before the host waits for a count
   cudaEvent_t ev[R];
   for (int j = 0; j < R; ++j) {
@@ -395,7 +425,8 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
     const int nxt = cur ^ 1;
     int tk = net ? prof_begin(net) : -1;
     k_coords<<<blocks_for(bound, 128), 128, 0, st>>>(r->ray[cur], r->next_k[cur], cap, &r->counters[cur], K,
-                                                     o.step, mv, r->coords, r->nvalid);
+                                                     o.step, o.step_max, o.alpha_exp, mv, r->coords, seg_exp,
+                                                     r->nvalid);
     if (net) prof_end(net, NV_K_OTHER, tk);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_coords launch")) != NV_OK) break;
     if (net) {
@@ -417,7 +448,7 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
     }
     tk = net ? prof_begin(net) : -1;
     k_composite<<<blocks_for(bound, 128), 128, 0, st>>>(
-        r->ray[cur], r->next_k[cur], cap, &r->counters[cur], r->values, r->nvalid, K, lut, o.alpha_exp, o.et,
+        r->ray[cur], r->next_k[cur], cap, &r->counters[cur], r->values, r->nvalid, seg_exp, K, lut, o.alpha_exp, o.et,
         r->ray[nxt], r->next_k[nxt], &r->counters[nxt], out, reinterpret_cast<unsigned long long *>(r->d_samples));
     if (net) prof_end(net, NV_K_RENDER, tk);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_composite launch")) != NV_OK) break;
@@ -466,7 +497,7 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
   if (e == cudaSuccess) e = cudaMemsetAsync(r.d_samples, 0, sizeof(int64_t), st);
   if (e != cudaSuccess) return nv_cuda_check(e, "render memset");
   float4 *out = reinterpret_cast<float4 *>(rgba);
-  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r.ray[0], r.next_k[0], cap, &r.counters[0], out);
+  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r.ray[0], r.next_k[0], cap, &r.counters[0], out, false);
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
   const McView mv = mc_view(mc);
@@ -480,15 +511,16 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
     if (it >= max_iter) return nv_fail(NV_ERR_STATE, "ray march did not finish within %lld iterations", (long long)max_iter);
     const int nxt = cur ^ 1;
     const int64_t bound = live;
-    k_coords<<<blocks_for(bound, 128), 128, 0, st>>>(r.ray[cur], r.next_k[cur], cap, &r.counters[cur], K, o.step, mv,
-                                                     r.coords, r.nvalid);
+    k_coords<<<blocks_for(bound, 128), 128, 0, st>>>(r.ray[cur], r.next_k[cur], cap, &r.counters[cur], K, o.step,
+                                                     0.f, o.alpha_exp, mv, r.coords, nullptr, r.nvalid);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_coords launch")) != NV_OK) return s;
     k_values_raw<<<blocks_for(bound * K, 256), 256, 0, st>>>(raw, r.coords, &r.counters[cur], K, r.values);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_values_raw launch")) != NV_OK) return s;
     if ((e = cudaMemsetAsync(&r.counters[nxt], 0, sizeof(int), st)) != cudaSuccess)
       return nv_cuda_check(e, "cudaMemsetAsync");
     k_composite<<<blocks_for(bound, 128), 128, 0, st>>>(
-        r.ray[cur], r.next_k[cur], cap, &r.counters[cur], r.values, r.nvalid, K, lut, o.alpha_exp, o.et, r.ray[nxt],
+        r.ray[cur], r.next_k[cur], cap, &r.counters[cur], r.values, r.nvalid, nullptr, K, lut, o.alpha_exp, o.et,
+        r.ray[nxt],
         r.next_k[nxt], &r.counters[nxt], out, reinterpret_cast<unsigned long long *>(r.d_samples));
     if ((s = nv_cuda_check(cudaGetLastError(), "k_composite launch")) != NV_OK) return s;
     if ((e = cudaMemcpyAsync(&live, &r.counters[nxt], sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

@@ -445,6 +445,7 @@ static void renderer_free(nv_renderer *r) {
   }
   cudaFree(r->coords);
   cudaFree(r->values);
+  cudaFree(r->seg_exp);
   cudaFree(r->nvalid);
   cudaFree(r->counters);
   cudaFree(r->d_samples);
@@ -469,6 +470,7 @@ extern "C" nv_status nv_renderer_create(int64_t max_pixels, int K, void *stream,
   }
   if (e == cudaSuccess) e = cudaMalloc(&r->coords, (size_t)max_pixels * K * 3 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&r->values, (size_t)max_pixels * K * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&r->seg_exp, (size_t)max_pixels * K * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&r->nvalid, (size_t)max_pixels * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&r->counters, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&r->d_samples, sizeof(int64_t));
@@ -504,6 +506,8 @@ extern "C" nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw
   if (opts->K != r->K) return nv_fail(NV_ERR_ARG, "nv_render: K=%d but the renderer was made for K=%d", opts->K, r->K);
   if (mc && (!mc->mu_max_dev || mc->cell < 1 || mc->nx < 1 || mc->ny < 1 || mc->nz < 1))
     return nv_fail(NV_ERR_ARG, "nv_render: bad macrocell grid");
+  if (opts->step_max > 0.f && (!mc || !(opts->step_max >= opts->step)))
+    return nv_fail(NV_ERR_ARG, "nv_render: the adaptive step needs macrocells and step_max >= step");
   if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render: tan_half_fovy < 0");
   return render_impl(r, net, raw, *cam, lut, mc, *opts, rgba);
 }
@@ -521,6 +525,7 @@ extern "C" nv_status nv_render_inshader(nv_ctx *net, const nv_camera *cam, const
     return nv_fail(NV_ERR_ARG, "nv_render_inshader: step, alpha_exp and et must be > 0");
   if (mc && (!mc->mu_max_dev || mc->cell < 1 || mc->nx < 1 || mc->ny < 1 || mc->nz < 1))
     return nv_fail(NV_ERR_ARG, "nv_render_inshader: bad macrocell grid");
+  if (opts->step_max > 0.f) return nv_fail(NV_ERR_UNSUPPORTED, "nv_render_inshader: no adaptive step");
   if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render_inshader: tan_half_fovy < 0");
   return render_inshader(net, *cam, lut, mc, *opts, rgba, reinterpret_cast<unsigned long long *>(samples_dev));
 }

@@ -74,6 +74,7 @@ struct nv_renderer {
   int *next_k[2];      // next sample index of each live ray
   float *coords;       // [max_pixels*K][3] sample positions of the current iteration
   float *values;       // [max_pixels*K] sample values
+  float *seg_exp;      // [max_pixels*K] opacity exponents of adaptive-step samples (NULL: fixed step only)
   int *nvalid;         // [max_pixels] valid samples of each ray this iteration
   int *counters;       // device: [0] live count (current), [1] live count (next)
   int *h_count;        // pinned host mirror of the live count

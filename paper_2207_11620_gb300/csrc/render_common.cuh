@@ -64,6 +64,57 @@ __device__ __forceinline__ int march_step(const float *o, const float *d, float 
   return kMarchSkip;
 }
 
+// Adaptive step (Sec. 5.3, Eq. 3), one step of the walk from the ray
+// parameter t, every FP32 operation rounded on its own as in the oracle.  The
+// cell is looked up just past the start (t + s1 / 1024), so a ray standing on
+// a face moves on into the next cell; the segment runs to the nearest of that
+// cell's exit, t1 and t + s_bar, s_bar = max(s1 + (s2 - s1) (1 - min(mu, 1))^2,
+// s1), and is at least s1 / 1024 long.  A transparent cell (mu == 0) is crossed
+// without a sample (kMarchSkip).  kMarchSample: pos = the segment midpoint and
+// e = alpha_exp * seg / s1, the opacity-correction exponent of its length;
+// t moves to the end of the segment.  Needs macrocells (mc.mu != NULL).
+__device__ __forceinline__ int march_step_adaptive(const float *o, const float *d, float t1, float s1, float s2,
+                                                   float alpha_exp, const McView &mc, float &t, float *pos,
+                                                   float &e) {
+  if (!(t < t1)) return kMarchEnd;
+  const float tiny = __fmul_rn(s1, 0.0009765625f);
+  const float tc = __fadd_rn(t, tiny);
+  const float sc[3] = {mc.sx, mc.sy, mc.sz};
+  const int nc[3] = {mc.ncx, mc.ncy, mc.ncz};
+  int c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = __fadd_rn(o[a], __fmul_rn(tc, d[a]));
+    c[a] = min(max((int)floorf(__fmul_rn(p, sc[a])), 0), nc[a] - 1);
+  }
+  float texit = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] != 0.f) {
+      const float face = __fdiv_rn((float)(d[a] > 0.f ? c[a] + 1 : c[a]), sc[a]);
+      texit = fminf(texit, __fdiv_rn(__fsub_rn(face, o[a]), d[a]));
+    }
+  }
+  texit = fminf(texit, t1);
+  float room = __fsub_rn(texit, t);
+  if (!(room > tiny)) room = tiny;
+  const float mu = __ldg(mc.mu + ((int64_t)c[2] * mc.ncy + c[1]) * mc.ncx + c[0]);
+  if (mu == 0.0f) {
+    t = __fadd_rn(t, room);
+    return kMarchSkip;
+  }
+  const float q = __fsub_rn(1.0f, fminf(mu, 1.0f));
+  const float grow = __fmul_rn(__fsub_rn(s2, s1), __fmul_rn(q, q));
+  const float sbar = fmaxf(__fadd_rn(s1, grow), s1);
+  const float seg = fminf(sbar, room);
+  const float tm = __fadd_rn(t, __fmul_rn(0.5f, seg));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pos[a] = __fadd_rn(o[a], __fmul_rn(tm, d[a]));
+  e = __fmul_rn(alpha_exp, __fdiv_rn(seg, s1));
+  t = __fadd_rn(t, seg);
+  return kMarchSample;
+}
+
 // A-14 for one sample value v: transfer function (linear between the 256 LUT
 // entries), opacity correction a' = 1 - (1 - a)^e, front-to-back compositing.
 // Returns true once the accumulated opacity reaches et (early termination).

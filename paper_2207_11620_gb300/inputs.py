@@ -108,6 +108,14 @@ def ramp_lut(alpha_floor: float = 0.0) -> np.ndarray:
     return np.ascontiguousarray(lut)
 
 
+def ramp_lut_soft(floor: float = 0.1) -> np.ndarray:
+    """256-entry RGBA LUT: colour i/255, opacity 0 up to `floor` and rising linearly
+    from there to 1 at entry 255 (no jump at the floor, unlike ramp_lut(alpha_floor))."""
+    r = np.arange(256, dtype=np.float32) / 255.0
+    a = np.clip((r - np.float32(floor)) / np.float32(1.0 - floor), 0.0, 1.0).astype(np.float32)
+    return np.ascontiguousarray(np.stack([r, r, r, a], axis=1).astype(np.float32))
+
+
 def ortho_camera_z(width: int, height: int) -> dict:
     """Orthographic camera looking along +z over the unit square (pixel centres)."""
     return dict(eye=(0.5, 0.5, -0.5), target=(0.5, 0.5, 0.5), up=(0.0, 1.0, 0.0),

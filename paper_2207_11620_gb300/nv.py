@@ -39,7 +39,8 @@ class Camera(C.Structure):
 
 
 class RenderOpts(C.Structure):
-    _fields_ = [("step", C.c_float), ("alpha_exp", C.c_float), ("et", C.c_float), ("K", C.c_int)]
+    _fields_ = [("step", C.c_float), ("alpha_exp", C.c_float), ("et", C.c_float), ("K", C.c_int),
+                ("step_max", C.c_float)]
 
 
 class Macrocells(C.Structure):
@@ -387,7 +388,7 @@ class Renderer:
         if out is None:
             out = torch.empty((c.height, c.width, 4), dtype=torch.float32, device="cuda")
         o = RenderOpts(float(opts["step"]), float(opts.get("alpha_exp", 1.0)), float(opts.get("et", 0.99)),
-                       int(opts.get("K", self.K)))
+                       int(opts.get("K", self.K)), float(opts.get("step_max", 0.0)))
         vp = C.byref(volume(raw)) if raw is not None else None
         mp = None
         if mc is not None:
@@ -438,7 +439,7 @@ def render_inshader(net: NeuralVolume, cam: dict, lut, opts: dict, mc: tuple | N
     if out is None:
         out = torch.empty((c.height, c.width, 4), dtype=torch.float32, device="cuda")
     o = RenderOpts(float(opts["step"]), float(opts.get("alpha_exp", 1.0)), float(opts.get("et", 0.99)),
-                   int(opts.get("K", 1)))
+                   int(opts.get("K", 1)), float(opts.get("step_max", 0.0)))
     mp = None
     if mc is not None:
         mu, cell, shape = mc
