@@ -34,7 +34,7 @@ UNIT = "samples/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "fp16", "bf16"])
@@ -478,13 +478,20 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
         is_img = torch.empty_like(img)
         is_img, is_ms = _median_frame_ms(
             torch, frames, lambda: nv.render_inshader(net, cam, lut, opts, mc=mc, out=is_img, samples=sam))
+        # adaptive step (Sec. 5.3, Eq. 3): s1 = the fixed step, s2 = one macrocell
+        ad_opts = dict(opts, step_max=opts["step"] * 2 * cfg["cell"])
+        ad_img, ad_ms = _time_render(r, torch, frames, cam=cam, lut=lut, opts=ad_opts, net=net, mc=mc)
+        ad_it, ad_ns = r.stats()
+        ad_psnr = _psnr(nv.image_mse(ad_img, raw).item())
         out[prec] = {"train_steps": steps, "train_ms_per_step": e0.elapsed_time(e1) / steps,
                      "frame_ms": ms, "samples_per_frame": ns, "iterations": it,
                      "decoded_samples_per_s": ns / (ms / 1e3), "image_psnr_db": _psnr(mse),
                      "volume_psnr_db": _psnr(net.volume_mse(vt).item()),
                      "inshader": {"frame_ms": is_ms, "samples_per_frame": int(sam.item()),
                                   "max_abs_diff_vs_streaming": float((is_img - img).abs().max().item()),
-                                  "streaming_speedup": is_ms / ms}}
+                                  "streaming_speedup": is_ms / ms},
+                     "adaptive_step": {"step_max_voxels": cfg["step_voxels"] * 2 * cfg["cell"], "frame_ms": ad_ms,
+                                       "samples_per_frame": ad_ns, "iterations": ad_it, "image_psnr_db": ad_psnr}}
         net.close()
     r.close()
     del vt
