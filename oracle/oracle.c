@@ -506,6 +506,9 @@ typedef struct {
   float et;        /* early-termination opacity */
   int mc_cell;     /* macrocell size in voxels (0: no empty-space skipping) */
   float step_max;  /* > 0: adaptive step (Sec. 5.3) between step and step_max; needs macrocells */
+  int shade;       /* 0: emission-absorption; 1: single-shot heuristic shadows */
+  float light[3];  /* unit direction towards the directional light (shade 1) */
+  float ambient;   /* shade 1: colour scale where the light is fully blocked */
 } or_opts;
 
 /* One step of the adaptive ray march (Sec. 5.3, Eq. 3) in FP32, every
@@ -648,30 +651,112 @@ static void or_tf(const float *lut, double v, double *rgba) {
   for (int c = 0; c < 4; ++c) rgba[c] = (1.0 - w) * (double)lut[4 * i + c] + w * (double)lut[4 * (i + 1) + c];
 }
 
-/* Sec. 5 / 5.2.1 / 5.3: emission-absorption ray march of selected pixels, one
- * ray at a time, every sample evaluated in order (the straightforward march
- * the streaming renderer is compared against, as the paper checks its
- * streaming path against a megakernel).  Samples sit at t_k = t0 +
- * (k + 1/2) step while t_k < t1; a sample whose macrocell has mu_max == 0 is
- * skipped; the value comes from the network (use_net) or from the raw volume
- * by trilinear interpolation; alpha is corrected as 1 - (1 - alpha)^(step/s1);
- * front-to-back: C += (1-A) alpha rgb, A += (1-A) alpha; the ray stops once
- * A >= et. */
+/* What one sample sees: the network (use_net) or the raw volume by trilinear
+ * interpolation. */
+typedef struct {
+  int use_net, L, F, log2T;
+  const int *res, *dims;
+  int n_dims;
+  const double *params, *weights;
+  const float *vol;
+  int nx, ny, nz;
+  const float *mumax;
+  int Ng, ncx, ncy, ncz;
+  float sx, sy, sz;
+} or_field;
+
+static double or_field_value(const or_field *f, const float *pos, double *act) {
+  if (f->use_net) {
+    or_encode_point(f->L, f->F, f->log2T, f->res, f->params, pos, act);
+    return or_mlp_point(f->dims, f->n_dims, f->weights, act);
+  }
+  return or_trilinear_point(f->vol, f->nx, f->ny, f->nz, pos);
+}
+
+/* The march of one ray from t0 to t1 (Sec. 5.2.1, 5.3).  Fixed step: samples
+ * at t_k = t0 + (k + 1/2) step while t_k < t1, a sample whose macrocell has
+ * mu_max == 0 skipped, opacity exponent alpha_exp.  Adaptive step
+ * (step_max > 0): the segments of or_march_adaptive_step.  Each sample's LUT
+ * opacity a is corrected to a' = 1 - (1 - a)^e.  transmit == 0: front-to-back
+ * compositing C += (1 - A) a' rgb, A += (1 - A) a', stop once A >= et; the
+ * sample with the largest contribution (1 - A) a' (the first of equals) is
+ * returned in best_pos / *best_w.  transmit != 0: only the opacity, A = 1 - T
+ * with T the product of (1 - a'), same stop. */
+static void or_march(const or_field *f, const float *lut, const or_opts *opt, const float *o, const float *d,
+                     float t0, float t1, int transmit, double *act, double *C, double *A, float *best_pos,
+                     double *best_w) {
+  double Ca[3] = {0, 0, 0}, Aa = 0.0, bw = 0.0;
+  float t = t0;
+  for (int64_t k = 0;; ++k) {
+    float pos[3];
+    double e = (double)opt->alpha_exp;
+    if (opt->step_max > 0.0f) {
+      float ef;
+      int r = or_march_adaptive_step(o, d, t1, opt->step, opt->step_max, opt->alpha_exp, f->mumax, f->ncx,
+                                     f->ncy, f->ncz, f->sx, f->sy, f->sz, &t, pos, &ef);
+      if (r == 0) break;
+      if (r == 2) continue;
+      e = (double)ef;
+    } else {
+      float tk = ((float)k + 0.5f) * opt->step;
+      tk = t0 + tk;
+      if (!(tk < t1)) break;
+      for (int a = 0; a < 3; ++a) { float s = tk * d[a]; pos[a] = o[a] + s; }
+      if (f->Ng > 0) {
+        int cx = (int)floorf(pos[0] * f->sx), cy = (int)floorf(pos[1] * f->sy), cz = (int)floorf(pos[2] * f->sz);
+        cx = cx < 0 ? 0 : (cx > f->ncx - 1 ? f->ncx - 1 : cx);
+        cy = cy < 0 ? 0 : (cy > f->ncy - 1 ? f->ncy - 1 : cy);
+        cz = cz < 0 ? 0 : (cz > f->ncz - 1 ? f->ncz - 1 : cz);
+        if (f->mumax[((int64_t)cz * f->ncy + cy) * f->ncx + cx] == 0.0f) continue;
+      }
+    }
+    double c[4];
+    or_tf(lut, or_field_value(f, pos, act), c);
+    double a = 1.0 - pow(1.0 - c[3], e);
+    double w = (1.0 - Aa) * a;
+    if (!transmit) {
+      for (int ch = 0; ch < 3; ++ch) Ca[ch] += w * c[ch];
+      if (w > bw) {
+        bw = w;
+        for (int q = 0; q < 3; ++q) best_pos[q] = pos[q];
+      }
+    }
+    Aa += w;
+    if (Aa >= (double)opt->et) break;
+  }
+  for (int ch = 0; ch < 3; ++ch) C[ch] = Ca[ch];
+  *A = Aa;
+  if (best_w) *best_w = bw;
+}
+
+/* Sec. 5, 5.2.1, 5.3: the ray march of selected pixels, one ray at a time, every
+ * sample evaluated in order (the straightforward march the streaming renderer
+ * is compared against, as the paper checks its streaming path against a
+ * megakernel).  shade 0: emission-absorption (or_march).  shade 1:
+ * single-shot heuristic shadows (Sec. 5: shading only at the point of highest
+ * contribution): after the primary march, a second march from that point
+ * towards the directional light (light = unit direction to it, clipped to the
+ * volume box, same sampling and opacity rules) gives its transmittance T, and
+ * the colour becomes C (ambient + (1 - ambient) T); A is kept.  A ray with no
+ * contribution casts no shadow ray. */
 void or_render_pixels(const or_camera *cam, const float *lut, const or_opts *opt,
                       int use_net, int L, int F, int log2T, const int *res, const int *dims, int n_dims,
                       const double *params,
                       const float *vol, int nx, int ny, int nz, const float *mumax,
                       const int64_t *pix, int64_t npix, double *rgba_out) {
-  int64_t T = (int64_t)1 << log2T;
-  const double *weights = use_net ? params + (int64_t)L * T * F : NULL;
-  int alen = use_net ? or_act_len(dims, n_dims) : 1;
-  int Ng = opt->mc_cell;
-  int ncx = 1, ncy = 1, ncz = 1;
-  float sx = 0.f, sy = 0.f, sz = 0.f;
-  if (Ng > 0) {
-    ncx = (nx + Ng - 1) / Ng; ncy = (ny + Ng - 1) / Ng; ncz = (nz + Ng - 1) / Ng;
-    sx = (float)nx / (float)Ng; sy = (float)ny / (float)Ng; sz = (float)nz / (float)Ng;
+  or_field f;
+  memset(&f, 0, sizeof(f));
+  f.use_net = use_net; f.L = L; f.F = F; f.log2T = log2T; f.res = res; f.dims = dims; f.n_dims = n_dims;
+  f.params = params;
+  f.weights = use_net ? params + (int64_t)L * ((int64_t)1 << log2T) * F : NULL;
+  f.vol = vol; f.nx = nx; f.ny = ny; f.nz = nz; f.mumax = mumax;
+  f.Ng = opt->mc_cell;
+  f.ncx = f.ncy = f.ncz = 1;
+  if (f.Ng > 0) {
+    f.ncx = (nx + f.Ng - 1) / f.Ng; f.ncy = (ny + f.Ng - 1) / f.Ng; f.ncz = (nz + f.Ng - 1) / f.Ng;
+    f.sx = (float)nx / (float)f.Ng; f.sy = (float)ny / (float)f.Ng; f.sz = (float)nz / (float)f.Ng;
   }
+  int alen = use_net ? or_act_len(dims, n_dims) : 1;
 #pragma omp parallel
   {
     double *act = (double *)malloc(sizeof(double) * alen);
@@ -682,56 +767,17 @@ void or_render_pixels(const or_camera *cam, const float *lut, const or_opts *opt
       float o[3], d[3], t0, t1;
       double C[3] = {0, 0, 0}, A = 0.0;
       or_ray(cam, px, py, o, d);
-      if (or_box(o, d, &t0, &t1) && opt->step_max > 0.0f) {
-        /* adaptive step (Sec. 5.3): segments from or_march_adaptive_step */
-        float t = t0;
-        for (;;) {
-          float pos[3], e;
-          int r = or_march_adaptive_step(o, d, t1, opt->step, opt->step_max, opt->alpha_exp, mumax, ncx, ncy,
-                                         ncz, sx, sy, sz, &t, pos, &e);
-          if (r == 0) break;
-          if (r == 2) continue;
-          double val;
-          if (use_net) {
-            or_encode_point(L, F, log2T, res, params, pos, act);
-            val = or_mlp_point(dims, n_dims, weights, act);
-          } else {
-            val = or_trilinear_point(vol, nx, ny, nz, pos);
-          }
-          double c[4];
-          or_tf(lut, val, c);
-          double a = 1.0 - pow(1.0 - c[3], (double)e);
-          for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * a * c[ch];
-          A += (1.0 - A) * a;
-          if (A >= (double)opt->et) break;
-        }
-      } else if (or_box(o, d, &t0, &t1)) {
-        for (int64_t k = 0;; ++k) {
-          float tk = ((float)k + 0.5f) * opt->step;
-          tk = t0 + tk;
-          if (!(tk < t1)) break;
-          float pos[3];
-          for (int a = 0; a < 3; ++a) { float s = tk * d[a]; pos[a] = o[a] + s; }
-          if (Ng > 0) {
-            int cx = (int)floorf(pos[0] * sx), cy = (int)floorf(pos[1] * sy), cz = (int)floorf(pos[2] * sz);
-            cx = cx < 0 ? 0 : (cx > ncx - 1 ? ncx - 1 : cx);
-            cy = cy < 0 ? 0 : (cy > ncy - 1 ? ncy - 1 : cy);
-            cz = cz < 0 ? 0 : (cz > ncz - 1 ? ncz - 1 : cz);
-            if (mumax[((int64_t)cz * ncy + cy) * ncx + cx] == 0.0f) continue;
-          }
-          double val;
-          if (use_net) {
-            or_encode_point(L, F, log2T, res, params, pos, act);
-            val = or_mlp_point(dims, n_dims, weights, act);
-          } else {
-            val = or_trilinear_point(vol, nx, ny, nz, pos);
-          }
-          double c[4];
-          or_tf(lut, val, c);
-          double a = 1.0 - pow(1.0 - c[3], (double)opt->alpha_exp);
-          for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * a * c[ch];
-          A += (1.0 - A) * a;
-          if (A >= (double)opt->et) break;
+      if (or_box(o, d, &t0, &t1)) {
+        float best[3] = {0, 0, 0};
+        double bw = 0.0;
+        or_march(&f, lut, opt, o, d, t0, t1, 0, act, C, &A, best, &bw);
+        if (opt->shade == 1 && bw > 0.0) {
+          float s0, s1;
+          double Cs[3], As = 0.0;
+          if (or_box(best, opt->light, &s0, &s1))
+            or_march(&f, lut, opt, best, opt->light, s0, s1, 1, act, Cs, &As, NULL, NULL);
+          double k = (double)opt->ambient + (1.0 - (double)opt->ambient) * (1.0 - As);
+          for (int ch = 0; ch < 3; ++ch) C[ch] *= k;
         }
       }
       rgba_out[4 * q + 0] = C[0];
@@ -741,6 +787,13 @@ void or_render_pixels(const or_camera *cam, const float *lut, const or_opts *opt
     }
     free(act);
   }
+}
+
+/* Exit distance of the ray o + t d (o inside the unit box) through the box,
+ * by the renderer's slab test; -1 if the test finds no interval. */
+float or_box_exit(const float *o, const float *d) {
+  float t0, t1;
+  return or_box(o, d, &t0, &t1) ? t1 : -1.0f;
 }
 
 /* Ray geometry of one pixel, exposed so tests can pin the camera model. */

@@ -45,7 +45,8 @@ class _Cam(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("step", C.c_float), ("alpha_exp", C.c_float), ("et", C.c_float),
-                ("mc_cell", C.c_int), ("step_max", C.c_float)]
+                ("mc_cell", C.c_int), ("step_max", C.c_float), ("shade", C.c_int),
+                ("light", C.c_float * 3), ("ambient", C.c_float)]
 
 
 _lib = None
@@ -100,6 +101,8 @@ def lib():
                                        C.c_int64, _f64p]
         L.or_pixel_ray.argtypes = [C.POINTER(_Cam), C.c_int, C.c_int, _f32p, _f32p, _f32p]
         L.or_pixel_ray.restype = C.c_int
+        L.or_box_exit.argtypes = [_f32p, _f32p]
+        L.or_box_exit.restype = C.c_float
         L.or_mse.argtypes = [_f64p, _f64p, C.c_int64]
         L.or_mse.restype = C.c_double
         L.or_psnr.argtypes = [C.c_double]
@@ -364,6 +367,10 @@ def pixel_ray(cam: dict, px, py):
     return bool(hit), o, d, t
 
 
+def box_exit(o, d):
+    return float(lib().or_box_exit(_f32(o), _f32(d)))
+
+
 def render_pixels(cam: dict, lut, opts: dict, pixels, net: Net | None = None, params=None,
                   vol=None, mumax=None):
     """RGBA (FP64) of the listed pixels; network values if net is given, else the raw volume.
@@ -375,6 +382,9 @@ def render_pixels(cam: dict, lut, opts: dict, pixels, net: Net | None = None, pa
     o.et = float(opts.get("et", 0.99))
     o.mc_cell = int(opts.get("mc_cell", 0))
     o.step_max = float(opts.get("step_max", 0.0))
+    o.shade = int(opts.get("shade", 0))
+    o.light = (C.c_float * 3)(*[float(v) for v in opts.get("light", (0.0, 0.0, 0.0))])
+    o.ambient = float(opts.get("ambient", 0.0))
     if o.step_max > 0 and o.mc_cell <= 0:
         raise ValueError("the adaptive step needs macrocells (mc_cell > 0)")
     pix = np.ascontiguousarray(pixels, dtype=np.int64)

@@ -516,6 +516,58 @@ def test_adaptive_step_without_adaptivity_is_the_midpoint_rule():
             assert e == pytest.approx(1.0, rel=1e-5)
 
 
+def _first_sample_shadow_closed_form(cam, lut, opts, vol, W, H, ambient, light):
+    # constant medium, fixed step: the first sample of every ray has the largest
+    # contribution, and the shadow march from it towards the light crosses N
+    # samples of the same opacity, N = #{k : fl32(fl32(k + 1/2) s) < L}
+    n = vol.shape[0]
+    a = float(lut[100, 3])
+    e = opts["alpha_exp"]
+    s = np.float32(opts["step"])
+    want = []
+    for p in range(W * H):
+        hit, o, d, t01 = O.pixel_ray(cam, p % W, p // W)
+        ks = np.arange(4 * n, dtype=np.float32)
+        tk = np.float32(t01[0]) + (ks + np.float32(0.5)) * s
+        M = int(np.count_nonzero(tk < t01[1]))
+        A = 1.0 - (1.0 - a) ** (e * M)
+        first = o + tk[0] * d
+        # distance from the first sample to the unit box along the light, per axis
+        Ls = [((1.0 if la > 0 else 0.0) - float(first[ax])) / la for ax, la in enumerate(light) if la != 0]
+        L = min(Ls)
+        N = int(np.count_nonzero((ks + np.float32(0.5)) * s < np.float32(L)))
+        T = (1.0 - a) ** (e * N)
+        k = ambient + (1.0 - ambient) * T
+        rgb = float(lut[100, 0]) * A
+        want.append([rgb * k, rgb * k, rgb * k, A])
+    return np.array(want)
+
+
+@pytest.mark.parametrize("light", [(1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (0.6, 0.0, -0.8)])
+def test_single_shot_shadow_constant_medium(light):
+    n = 24
+    vol = np.full((n, n, n), np.float32(100.0 / 255.0), np.float32)
+    lut = I.ramp_lut()
+    W, H = 7, 5
+    cam = I.ortho_camera_z(W, H)
+    opts = dict(step=0.5 / n, alpha_exp=0.5, et=2.0, shade=1, light=light, ambient=0.2)
+    got = O.render_pixels(cam, lut, opts, np.arange(W * H), vol=vol)
+    want = _first_sample_shadow_closed_form(cam, lut, opts, vol, W, H, 0.2, light)
+    np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9)
+    # the shadow only darkens: the emission-absorption image is the bound
+    ea = O.render_pixels(cam, lut, dict(opts, shade=0), np.arange(W * H), vol=vol)
+    assert np.all(got[:, :3] <= ea[:, :3] + 1e-12) and np.all(got[:, 3] == ea[:, 3])
+
+
+def test_single_shot_shadow_empty_volume_casts_nothing():
+    vol = np.zeros((16, 16, 16), np.float32)
+    lut = I.ramp_lut(alpha_floor=0.1)
+    cam = I.perspective_camera(6, 6)
+    opts = dict(step=0.5 / 16, alpha_exp=0.5, et=0.99, shade=1, light=(0.0, 1.0, 0.0), ambient=0.3)
+    got = O.render_pixels(cam, lut, opts, np.arange(36), vol=vol)
+    assert np.all(got == 0)
+
+
 def test_ortho_rays_through_pixel_centres():
     cam = I.ortho_camera_z(64, 64)
     for px, py in [(0, 0), (17, 40), (63, 63)]:
