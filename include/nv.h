@@ -85,6 +85,9 @@ typedef struct {
   int K;           /* samples streamed per live ray per iteration (Sec. 5.2.1; ~8) */
   float step_max;  /* > 0: adaptive step (Sec. 5.3, Eq. 3) between `step` (s1) and step_max (s2), p = 2;
                       needs macrocells; 0: fixed step */
+  int shade;       /* 0: emission-absorption; 1: single-shot heuristic shadows (Sec. 5) */
+  float light[3];  /* shade 1: unit direction towards the directional light */
+  float ambient;   /* shade 1: colour scale where the light is fully blocked, in [0, 1] */
 } nv_render_opts;
 
 typedef struct {
@@ -263,7 +266,12 @@ nv_status nv_renderer_destroy(nv_renderer *r);
  * each segment takes s_bar = max(s1 + (s2 - s1) (1 - min(mu, 1))^2, s1) from
  * the macrocell it starts in, ends at that cell's face, t1 or s_bar, samples
  * its midpoint and corrects the opacity by its own length; transparent cells
- * are crossed without samples. */
+ * are crossed without samples.  opts->shade == 1 adds single-shot heuristic
+ * shadows (Sec. 5): the ray remembers its sample of largest contribution
+ * (1 - A) a' and, when its march ends, marches on from that point towards the
+ * light (clipped to the volume box, same sampling rules, opacity only); the
+ * colour becomes C (ambient + (1 - ambient) T) with T that march's
+ * transmittance, A is kept.  A ray with no contribution casts no shadow ray. */
 nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
                     const float *lut_dev, const nv_macrocells *mc, const nv_render_opts *opts,
                     float *rgba_dev);

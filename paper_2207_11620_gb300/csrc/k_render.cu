@@ -162,9 +162,10 @@ __device__ __forceinline__ int warp_append(int *counter, bool pred) {
   return base + __popc(mask & ((1u << lane) - 1u));
 }
 
-// next_k starts at sample 0, or, for the adaptive step, at the ray parameter t0 (float bits).
+// next_k starts at sample 0, or, for the adaptive step, at the ray parameter t0
+// (float bits); aux (nullable) gets the initial single-shot shadow state.
 __global__ void k_raygen(nv_camera cam, float *ray, int *next_k, int64_t cap, int *count, float4 *rgba,
-                         bool adaptive) {
+                         bool adaptive, float *aux) {
   const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t npix = (int64_t)cam.width * cam.height;
   bool hit = false;
@@ -190,6 +191,10 @@ __global__ void k_raygen(nv_camera cam, float *ray, int *next_k, int64_t cap, in
     ray[R_CA * cap + slot] = 0.f;
     ray[R_PIX * cap + slot] = __int_as_float((int)pix);
     next_k[slot] = adaptive ? __float_as_int(t0) : 0;
+    if (aux) {
+      aux[AUX_BW * cap + slot] = 0.f;
+      aux[AUX_AS * cap + slot] = -1.f;  // primary march
+    }
   }
 }
 
@@ -259,29 +264,91 @@ __global__ void k_values_raw(nv_volume v, const float *__restrict__ coords, cons
 __global__ void k_composite(const float *__restrict__ ray, const int *__restrict__ next_k_in, int64_t cap,
                             const int *count, const float *__restrict__ values, const int *__restrict__ nvalid,
                             const float *__restrict__ seg_exp, int K, const float *__restrict__ lut,
-                            float alpha_exp, float et, float *ray_out,
-                            int *next_k_out, int *count_out, float4 *rgba, unsigned long long *samples) {
+                            float alpha_exp, float et, ShadeArgs sh, const float *__restrict__ coords,
+                            const float *__restrict__ aux, float *aux_out, float *ray_out, int *next_k_out,
+                            int *count_out, float4 *rgba, unsigned long long *samples) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int n = *count;
   bool live = false;
   int nv = 0;
   float cr = 0.f, cg = 0.f, cb = 0.f, ca = 0.f;
+  float geo[8];  // o, d, t0, t1 of the ray that continues
+  int nk = 0;
+  float bw = 0.f, bp[3] = {0.f, 0.f, 0.f}, as = -1.f;
   if (i < n) {
     cr = ray[R_CR * cap + i];
     cg = ray[R_CG * cap + i];
     cb = ray[R_CB * cap + i];
     ca = ray[R_CA * cap + i];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) geo[f] = ray[(R_OX + f) * cap + i];
+    nk = next_k_in[i];
     nv = nvalid[i];
-    bool done = false;
-    for (int j = 0; j < nv; ++j) {
-      const float ex = seg_exp ? seg_exp[i * K + j] : alpha_exp;
-      if (composite_one(values[i * K + j], lut, ex, et, cr, cg, cb, ca)) {
-        done = true;
-        break;
-      }
+    if (sh.on) {
+      bw = aux[AUX_BW * cap + i];
+      bp[0] = aux[AUX_BX * cap + i];
+      bp[1] = aux[AUX_BY * cap + i];
+      bp[2] = aux[AUX_BZ * cap + i];
+      as = aux[AUX_AS * cap + i];
     }
-    if (nv < K) done = true;  // the ray left the volume during this batch
-    if (done) rgba[__float_as_int(ray[R_PIX * cap + i])] = make_float4(cr, cg, cb, ca);
+    bool done = false;
+    if (as < 0.f) {  // the primary march (A-14)
+      for (int j = 0; j < nv; ++j) {
+        const float ex = seg_exp ? seg_exp[i * K + j] : alpha_exp;
+        float w;
+        const bool stop = composite_one(values[i * K + j], lut, ex, et, cr, cg, cb, ca, &w);
+        if (sh.on && w > bw) {
+          bw = w;
+          const float *p = coords + (i * K + j) * 3;
+          bp[0] = p[0];
+          bp[1] = p[1];
+          bp[2] = p[2];
+        }
+        if (stop) {
+          done = true;
+          break;
+        }
+      }
+      if (nv < K) done = true;  // the ray left the volume during this batch
+      if (done && sh.on && bw > 0.f) {
+        // single-shot shadow: march on from the sample of largest contribution
+        float s0, s1;
+        if (nv_box(bp, sh.light, s0, s1)) {
+          geo[0] = bp[0];
+          geo[1] = bp[1];
+          geo[2] = bp[2];
+          geo[3] = sh.light[0];
+          geo[4] = sh.light[1];
+          geo[5] = sh.light[2];
+          geo[6] = s0;
+          geo[7] = s1;
+          nk = seg_exp ? __float_as_int(s0) : 0;
+          as = 0.f;
+          done = false;
+        }
+      }
+    } else {  // the shadow march: opacity only
+      for (int j = 0; j < nv; ++j) {
+        const float ex = seg_exp ? seg_exp[i * K + j] : alpha_exp;
+        float r, g, b, ac;
+        tf_lookup(values[i * K + j], lut, ex, r, g, b, ac);
+        as += (1.0f - as) * ac;
+        if (as >= et) {
+          done = true;
+          break;
+        }
+      }
+      if (nv < K) done = true;
+    }
+    if (done) {
+      if (as >= 0.f) {  // shaded at the point of largest contribution
+        const float k = sh.ambient + (1.0f - sh.ambient) * (1.0f - as);
+        cr *= k;
+        cg *= k;
+        cb *= k;
+      }
+      rgba[__float_as_int(ray[R_PIX * cap + i])] = make_float4(cr, cg, cb, ca);
+    }
     live = !done;
   }
   // evaluated samples of this warp, for the statistics
@@ -292,13 +359,20 @@ __global__ void k_composite(const float *__restrict__ ray, const int *__restrict
   const int slot = warp_append(count_out, live);
   if (live) {
 #pragma unroll
-    for (int f = R_OX; f <= R_T1; ++f) ray_out[f * cap + slot] = ray[f * cap + i];
+    for (int f = 0; f < 8; ++f) ray_out[(R_OX + f) * cap + slot] = geo[f];
     ray_out[R_CR * cap + slot] = cr;
     ray_out[R_CG * cap + slot] = cg;
     ray_out[R_CB * cap + slot] = cb;
     ray_out[R_CA * cap + slot] = ca;
     ray_out[R_PIX * cap + slot] = ray[R_PIX * cap + i];
-    next_k_out[slot] = next_k_in[i];
+    next_k_out[slot] = nk;
+    if (sh.on) {
+      aux_out[AUX_BW * cap + slot] = bw;
+      aux_out[AUX_BX * cap + slot] = bp[0];
+      aux_out[AUX_BY * cap + slot] = bp[1];
+      aux_out[AUX_BZ * cap + slot] = bp[2];
+      aux_out[AUX_AS * cap + slot] = as;
+    }
   }
 }
 
@@ -398,8 +472,9 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   float4 *out = reinterpret_cast<float4 *>(rgba);
   const bool adaptive = o.step_max > 0.f;
   float *seg_exp = adaptive ? r->seg_exp : nullptr;
+  ShadeArgs sh{o.shade, {o.light[0], o.light[1], o.light[2]}, o.ambient};
   k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r->ray[0], r->next_k[0], cap, &r->counters[0], out,
-                                                  adaptive);
+                                                  adaptive, sh.on ? r->aux[0] : nullptr);
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
 
@@ -408,7 +483,8 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   // adaptive segments also end at every cell face a ray crosses
   int64_t max_samples = (int64_t)std::ceil(1.7320509 / (double)o.step);
   if (adaptive) max_samples = max_samples * 1025 / 1024 + 3 * (int64_t)(mv.ncx + mv.ncy + mv.ncz) + 8;
-  const int64_t max_iter = (max_samples + K - 1) / K + 4;
+  // a shadow march follows the primary one
+  const int64_t max_iter = (sh.on ? 2 : 1) * ((max_samples + K - 1) / K + 4);
   const int R = 4;  // iterations in flight before the host waits for a count
   cudaEvent_t ev[R];
   for (int j = 0; j < R; ++j) {
@@ -449,7 +525,8 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
     tk = net ? prof_begin(net) : -1;
     k_composite<<<blocks_for(bound, 128), 128, 0, st>>>(
         r->ray[cur], r->next_k[cur], cap, &r->counters[cur], r->values, r->nvalid, seg_exp, K, lut, o.alpha_exp, o.et,
-        r->ray[nxt], r->next_k[nxt], &r->counters[nxt], out, reinterpret_cast<unsigned long long *>(r->d_samples));
+        sh, r->coords, r->aux[cur], r->aux[nxt], r->ray[nxt], r->next_k[nxt], &r->counters[nxt], out,
+        reinterpret_cast<unsigned long long *>(r->d_samples));
     if (net) prof_end(net, NV_K_RENDER, tk);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_composite launch")) != NV_OK) break;
     const int slot = (int)(issued % R);
@@ -497,7 +574,8 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
   if (e == cudaSuccess) e = cudaMemsetAsync(r.d_samples, 0, sizeof(int64_t), st);
   if (e != cudaSuccess) return nv_cuda_check(e, "render memset");
   float4 *out = reinterpret_cast<float4 *>(rgba);
-  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r.ray[0], r.next_k[0], cap, &r.counters[0], out, false);
+  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r.ray[0], r.next_k[0], cap, &r.counters[0], out, false,
+                                                  nullptr);
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
   const McView mv = mc_view(mc);
@@ -520,7 +598,7 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
       return nv_cuda_check(e, "cudaMemsetAsync");
     k_composite<<<blocks_for(bound, 128), 128, 0, st>>>(
         r.ray[cur], r.next_k[cur], cap, &r.counters[cur], r.values, r.nvalid, nullptr, K, lut, o.alpha_exp, o.et,
-        r.ray[nxt],
+        ShadeArgs{}, r.coords, nullptr, nullptr, r.ray[nxt],
         r.next_k[nxt], &r.counters[nxt], out, reinterpret_cast<unsigned long long *>(r.d_samples));
     if ((s = nv_cuda_check(cudaGetLastError(), "k_composite launch")) != NV_OK) return s;
     if ((e = cudaMemcpyAsync(&live, &r.counters[nxt], sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

@@ -446,6 +446,8 @@ static void renderer_free(nv_renderer *r) {
   cudaFree(r->coords);
   cudaFree(r->values);
   cudaFree(r->seg_exp);
+  cudaFree(r->aux[0]);
+  cudaFree(r->aux[1]);
   cudaFree(r->nvalid);
   cudaFree(r->counters);
   cudaFree(r->d_samples);
@@ -471,6 +473,7 @@ extern "C" nv_status nv_renderer_create(int64_t max_pixels, int K, void *stream,
   if (e == cudaSuccess) e = cudaMalloc(&r->coords, (size_t)max_pixels * K * 3 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&r->values, (size_t)max_pixels * K * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&r->seg_exp, (size_t)max_pixels * K * sizeof(float));
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&r->aux[b], (size_t)max_pixels * 5 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&r->nvalid, (size_t)max_pixels * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&r->counters, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&r->d_samples, sizeof(int64_t));
@@ -508,6 +511,12 @@ extern "C" nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw
     return nv_fail(NV_ERR_ARG, "nv_render: bad macrocell grid");
   if (opts->step_max > 0.f && (!mc || !(opts->step_max >= opts->step)))
     return nv_fail(NV_ERR_ARG, "nv_render: the adaptive step needs macrocells and step_max >= step");
+  if (opts->shade != 0 && opts->shade != 1) return nv_fail(NV_ERR_ARG, "nv_render: shade=%d", opts->shade);
+  if (opts->shade == 1) {
+    const float l2 = opts->light[0] * opts->light[0] + opts->light[1] * opts->light[1] + opts->light[2] * opts->light[2];
+    if (!(fabsf(l2 - 1.f) < 1e-3f) || !(opts->ambient >= 0.f && opts->ambient <= 1.f))
+      return nv_fail(NV_ERR_ARG, "nv_render: shadows need a unit light direction and ambient in [0, 1]");
+  }
   if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render: tan_half_fovy < 0");
   return render_impl(r, net, raw, *cam, lut, mc, *opts, rgba);
 }
@@ -525,7 +534,8 @@ extern "C" nv_status nv_render_inshader(nv_ctx *net, const nv_camera *cam, const
     return nv_fail(NV_ERR_ARG, "nv_render_inshader: step, alpha_exp and et must be > 0");
   if (mc && (!mc->mu_max_dev || mc->cell < 1 || mc->nx < 1 || mc->ny < 1 || mc->nz < 1))
     return nv_fail(NV_ERR_ARG, "nv_render_inshader: bad macrocell grid");
-  if (opts->step_max > 0.f) return nv_fail(NV_ERR_UNSUPPORTED, "nv_render_inshader: no adaptive step");
+  if (opts->step_max > 0.f || opts->shade != 0)
+    return nv_fail(NV_ERR_UNSUPPORTED, "nv_render_inshader: emission-absorption with the fixed step only");
   if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render_inshader: tan_half_fovy < 0");
   return render_inshader(net, *cam, lut, mc, *opts, rgba, reinterpret_cast<unsigned long long *>(samples_dev));
 }

@@ -75,6 +75,7 @@ struct nv_renderer {
   float *coords;       // [max_pixels*K][3] sample positions of the current iteration
   float *values;       // [max_pixels*K] sample values
   float *seg_exp;      // [max_pixels*K] opacity exponents of adaptive-step samples (NULL: fixed step only)
+  float *aux[2];       // [5][max_pixels] single-shot shadow state, ping-pong with ray (NULL: no shadows)
   int *nvalid;         // [max_pixels] valid samples of each ray this iteration
   int *counters;       // device: [0] live count (current), [1] live count (next)
   int *h_count;        // pinned host mirror of the live count

@@ -86,7 +86,8 @@ extern "C" nv_status nv_render_raw_noalloc(const nv_volume *raw, const nv_camera
   if (!(opts->step > 0.f) || !(opts->alpha_exp > 0.f) || !(opts->et > 0.f))
     return nv_fail(NV_ERR_ARG, "nv_render_raw_noalloc: step, alpha_exp and et must be > 0");
   if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render_raw_noalloc: tan_half_fovy < 0");
-  if (opts->step_max > 0.f) return nv_fail(NV_ERR_UNSUPPORTED, "nv_render_raw_noalloc: no adaptive step");
+  if (opts->step_max > 0.f || opts->shade != 0)
+    return nv_fail(NV_ERR_UNSUPPORTED, "nv_render_raw_noalloc: emission-absorption with the fixed step only");
   if (mc && (!mc->mu_max_dev || mc->cell < 1 || mc->nx < 1 || mc->ny < 1 || mc->nz < 1))
     return nv_fail(NV_ERR_ARG, "nv_render_raw_noalloc: bad macrocell grid");
   unsigned char *base = nullptr;

@@ -118,21 +118,41 @@ __device__ __forceinline__ int march_step_adaptive(const float *o, const float *
 // A-14 for one sample value v: transfer function (linear between the 256 LUT
 // entries), opacity correction a' = 1 - (1 - a)^e, front-to-back compositing.
 // Returns true once the accumulated opacity reaches et (early termination).
-__device__ __forceinline__ bool composite_one(float v, const float *__restrict__ lut, float alpha_exp, float et,
-                                              float &cr, float &cg, float &cb, float &ca) {
+__device__ __forceinline__ void tf_lookup(float v, const float *__restrict__ lut, float alpha_exp, float &r,
+                                          float &g, float &b, float &ac) {
   const float u = __fmul_rn(fminf(fmaxf(v, 0.f), 1.f), 255.0f);
   const int e = min((int)floorf(u), 254);
   const float w = u - (float)e;
   const float4 l0 = __ldg(reinterpret_cast<const float4 *>(lut) + e);
   const float4 l1 = __ldg(reinterpret_cast<const float4 *>(lut) + e + 1);
-  const float r = l0.x + w * (l1.x - l0.x), g = l0.y + w * (l1.y - l0.y), b = l0.z + w * (l1.z - l0.z);
+  r = l0.x + w * (l1.x - l0.x);
+  g = l0.y + w * (l1.y - l0.y);
+  b = l0.z + w * (l1.z - l0.z);
   const float al = l0.w + w * (l1.w - l0.w);
   // a' = 1 - (1 - a)^e, as -expm1(e log1p(-a)) to keep small opacities accurate
-  const float ac = (alpha_exp == 1.0f) ? al : -expm1f(alpha_exp * log1pf(-al));
+  ac = (alpha_exp == 1.0f) ? al : -expm1f(alpha_exp * log1pf(-al));
+}
+
+// w (nullable) receives the sample's contribution (1 - A) a'.
+__device__ __forceinline__ bool composite_one(float v, const float *__restrict__ lut, float alpha_exp, float et,
+                                              float &cr, float &cg, float &cb, float &ca, float *w = nullptr) {
+  float r, g, b, ac;
+  tf_lookup(v, lut, alpha_exp, r, g, b, ac);
   const float tr = (1.0f - ca) * ac;
   cr += tr * r;
   cg += tr * g;
   cb += tr * b;
   ca += tr;
+  if (w) *w = tr;
   return ca >= et;
 }
+
+// Single-shot heuristic shadows (Sec. 5): per-ray state beside the ray
+// buffers, [kAuxN][cap] floats: the best contribution so far, its position,
+// and the opacity of the shadow march (negative during the primary march).
+enum { AUX_BW = 0, AUX_BX, AUX_BY, AUX_BZ, AUX_AS, kAuxN };
+struct ShadeArgs {
+  int on;          // 1: single-shot shadows
+  float light[3];  // unit direction towards the directional light
+  float ambient;   // colour scale where the light is fully blocked
+};

@@ -40,7 +40,16 @@ class Camera(C.Structure):
 
 class RenderOpts(C.Structure):
     _fields_ = [("step", C.c_float), ("alpha_exp", C.c_float), ("et", C.c_float), ("K", C.c_int),
-                ("step_max", C.c_float)]
+                ("step_max", C.c_float), ("shade", C.c_int), ("light", C.c_float * 3), ("ambient", C.c_float)]
+
+
+def render_opts(opts: dict, K: int) -> RenderOpts:
+    """nv_render_opts from a dict: step, alpha_exp (1), et (0.99), K, step_max (0 = fixed step),
+    shade (0 = emission-absorption, 1 = single-shot shadows), light (unit direction to it), ambient."""
+    return RenderOpts(float(opts["step"]), float(opts.get("alpha_exp", 1.0)), float(opts.get("et", 0.99)),
+                      int(opts.get("K", K)), float(opts.get("step_max", 0.0)), int(opts.get("shade", 0)),
+                      (C.c_float * 3)(*[float(v) for v in opts.get("light", (0.0, 0.0, 0.0))]),
+                      float(opts.get("ambient", 0.0)))
 
 
 class Macrocells(C.Structure):
@@ -387,8 +396,7 @@ class Renderer:
         c = camera(cam)
         if out is None:
             out = torch.empty((c.height, c.width, 4), dtype=torch.float32, device="cuda")
-        o = RenderOpts(float(opts["step"]), float(opts.get("alpha_exp", 1.0)), float(opts.get("et", 0.99)),
-                       int(opts.get("K", self.K)), float(opts.get("step_max", 0.0)))
+        o = render_opts(opts, self.K)
         vp = C.byref(volume(raw)) if raw is not None else None
         mp = None
         if mc is not None:
@@ -438,8 +446,7 @@ def render_inshader(net: NeuralVolume, cam: dict, lut, opts: dict, mc: tuple | N
     c = camera(cam)
     if out is None:
         out = torch.empty((c.height, c.width, 4), dtype=torch.float32, device="cuda")
-    o = RenderOpts(float(opts["step"]), float(opts.get("alpha_exp", 1.0)), float(opts.get("et", 0.99)),
-                   int(opts.get("K", 1)), float(opts.get("step_max", 0.0)))
+    o = render_opts(opts, 1)
     mp = None
     if mc is not None:
         mu, cell, shape = mc

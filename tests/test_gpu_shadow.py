@@ -1,0 +1,115 @@
+"""GPU parity of ray marching with single-shot heuristic shadows (Sec. 5)
+against the oracle: the primary march, the choice of the sample of largest
+contribution and the shadow march from it follow the same FP32 positions; the
+values follow the FP32 tolerance.  A pixel whose largest contribution is a
+near tie may pick the other sample on one side, which moves its shadow: such
+pixels are counted and must be rare."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2207_11620_gb300 import configs as CF
+from paper_2207_11620_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def nv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_11620_gb300 import build, nv as nvmod
+    build.build()
+    return nvmod
+
+
+def _compare(got, want, max_frac=0.01):
+    got = got.reshape(-1, 4).astype(np.float64)
+    den = np.maximum(np.abs(want), 1e-2 * max(np.abs(want).max(), 1e-30))
+    bad = (np.abs(got - want) / den > TOL).any(axis=1)
+    assert bad.mean() <= max_frac, (bad.sum(), len(bad))
+    # the opacity channel is the emission-absorption one: unaffected by the shadow choice
+    term = np.maximum(got[:, 3], want[:, 3]) >= 0.99 - 1e-4
+    a_bad = (np.abs(got[:, 3] - want[:, 3]) / den[:, 3] > TOL) & ~term
+    assert not a_bad.any()
+    return int(bad.sum())
+
+
+@pytest.mark.parametrize("light", [(0.0, 1.0, 0.0), (0.48, 0.6, -0.64)])
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_shadow_raw_volume_matches_oracle(nv, light, adaptive):
+    vol = I.blob_volume((40, 48, 56), seed=4)
+    vt = torch.from_numpy(vol).cuda()
+    lut = I.ramp_lut_soft(0.1)
+    lt = torch.from_numpy(lut).cuda()
+    _, mu = nv.macrocells_build(vt, 8, lt)
+    s1 = 0.5 / 56
+    opts = dict(step=s1, alpha_exp=0.5, et=0.99, K=8, mc_cell=8, shade=1, light=light, ambient=0.25)
+    if adaptive:
+        opts["step_max"] = 16 * s1
+    cam = I.perspective_camera(72, 54)
+    r = nv.Renderer(72 * 54, K=8)
+    img = r.render(cam, lt, opts, raw=vt, mc=(mu, 8, vol.shape)).cpu().numpy()
+    want = O.render_pixels(cam, lut, opts, np.arange(72 * 54), vol=vol, mumax=mu.cpu().numpy())
+    _compare(img, want)
+    ea = r.render(cam, lt, dict(opts, shade=0), raw=vt, mc=(mu, 8, vol.shape)).cpu().numpy().reshape(-1, 4)
+    assert np.all(img.reshape(-1, 4)[:, :3] <= ea[:, :3] + 1e-6)
+    assert (img.reshape(-1, 4)[:, :3] < ea[:, :3] * 0.9).any()  # some light is blocked
+
+
+def test_shadow_constant_medium_closed_form(nv):
+    n = 24
+    vol = np.full((n, n, n), np.float32(100.0 / 255.0), np.float32)
+    lut = I.ramp_lut()
+    W, H = 7, 5
+    cam = I.ortho_camera_z(W, H)
+    opts = dict(step=0.5 / n, alpha_exp=0.5, et=2.0, K=4, shade=1, light=(1.0, 0.0, 0.0), ambient=0.2)
+    img = nv.Renderer(W * H, K=4).render(cam, torch.from_numpy(lut).cuda(), opts,
+                                         raw=torch.from_numpy(vol).cuda()).cpu().numpy().reshape(-1, 4)
+    a = float(lut[100, 3])
+    s = np.float32(opts["step"])
+    ks = np.arange(4 * n, dtype=np.float32)
+    for p in range(W * H):
+        hit, o, d, t01 = O.pixel_ray(cam, p % W, p // W)
+        tk = np.float32(t01[0]) + (ks + np.float32(0.5)) * s
+        M = int(np.count_nonzero(tk < t01[1]))
+        first = o + tk[0] * d
+        N = int(np.count_nonzero((ks + np.float32(0.5)) * s < np.float32(1.0 - float(first[0]))))
+        A = 1.0 - (1.0 - a) ** (0.5 * M)
+        k = 0.2 + 0.8 * (1.0 - a) ** (0.5 * N)
+        assert img[p, 3] == pytest.approx(A, rel=1e-5)
+        assert img[p, 0] == pytest.approx(float(lut[100, 0]) * A * k, rel=1e-4)
+
+
+def test_shadow_network_fp32_matches_oracle(nv):
+    c = CF.CFG2_NET
+    net = nv.NeuralVolume(prec="fp32", **c.kwargs())
+    params = I.init_params(net.n_table, net.n_params - net.n_table, seed=7, dims=c.dims)
+    params[: net.n_table] = I.uniform_params(net.n_table, seed=8, scale=0.5)
+    net.set_params(params)
+    vol = I.blob_volume(32, seed=5)
+    lut = I.ramp_lut_soft(0.1)
+    lt = torch.from_numpy(lut).cuda()
+    _, mu = nv.macrocells_build(torch.from_numpy(vol).cuda(), 8, lt)
+    opts = dict(step=0.5 / 32, alpha_exp=0.5, et=0.99, K=8, mc_cell=8, shade=1, light=(0.0, 0.8, 0.6),
+                ambient=0.3)
+    cam = I.perspective_camera(40, 32)
+    img = nv.Renderer(40 * 32, K=8).render(cam, lt, opts, net=net, mc=(mu, 8, vol.shape)).cpu().numpy()
+    pix = np.random.default_rng(2).choice(40 * 32, 300, replace=False)
+    want = O.render_pixels(cam, lut, opts, pix, net=onet(c), params=params, vol=vol, mumax=mu.cpu().numpy())
+    _compare(img.reshape(-1, 4)[pix], want, max_frac=0.02)
+
+
+def onet(c):
+    return O.Net(L=c.L, F=c.F, log2T=c.log2T, Nmin=c.Nmin, b=c.b, dims=c.dims)
+
+
+def test_shadow_rejects_bad_light(nv):
+    vt = torch.from_numpy(I.blob_volume(16, seed=1)).cuda()
+    lt = torch.from_numpy(I.ramp_lut()).cuda()
+    r = nv.Renderer(64, K=8)
+    with pytest.raises(nv.NvError, match="unit light"):
+        r.render(I.ortho_camera_z(8, 8), lt, dict(step=1 / 64, shade=1, light=(0.0, 2.0, 0.0)), raw=vt)
