@@ -880,3 +880,241 @@ void or_brick_sample(const float *vol, int nx, int ny, int nz, int B, const int 
     target[i] = or_trilinear_point(vol, nx, ny, nz, xyz + 3 * i);
   }
 }
+
+/* ------------------------------------------------------- path tracing -- */
+
+/* Volumetric path tracing (Sec. 5.2.2, Alg. 1, Eq. 1-2), one path per pixel
+ * and frame, as a plain loop.  Readings (the paper names the method, not its
+ * constants): extinction sigma(x) = D a(v(x)) per unit length with a the
+ * transfer function's opacity and D a density scale; single-scattering albedo
+ * = the transfer function's colour; isotropic phase function; one directional
+ * light towards `light` whose irradiance cancels the phase factor (a visible
+ * light adds throughput * albedo); the background is black.  Free flights use
+ * Woodcock tracking with the majorant of each macrocell (Hofmann): the target
+ * optical thickness tau = -log(1 - zeta) is spent cell by cell along the ray
+ * (tau_n = sum of D mu_max_i s_i), the tentative collision is stepped back into
+ * the cell where tau_n first exceeds it, and accepted with probability
+ * sigma(x) / (D mu_max_cell); a null collision restarts the flight there.  At
+ * every real collision a shadow ray towards the light is tracked the same way
+ * (visible when it leaves the volume without a real collision), then the
+ * throughput is multiplied by the albedo, Russian roulette from bounce 3
+ * keeps the path with probability min(1, max throughput), and an isotropic
+ * direction is drawn; paths end on leaving the volume or after max_bounces
+ * real collisions.
+ * Random numbers: Philox4x32-10 with key = seed and counter = (pixel, event,
+ * frame, 0); every flight and every scattering event draws one block of four.
+ * The branch decisions (cell walk, collision point, acceptance, roulette) are
+ * taken in FP32, every operation rounded on its own, as the GPU takes them --
+ * for the raw volume the density is evaluated the same way -- so both sides
+ * follow the same paths; -log(1 - zeta) and the direction's trigonometry are
+ * evaluated in FP64 and rounded to FP32. */
+
+typedef struct {
+  float density;     /* D */
+  float light[3];    /* unit direction towards the light */
+  int max_bounces;
+  uint32_t seed_lo, seed_hi;
+  uint32_t frame;
+} or_pt_opts;
+
+static const float OR_PT_TINY = 9.5367431640625e-07f; /* 2^-20: cell lookups just past a position */
+
+static float or_u01(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-08f; }
+
+/* FP32 trilinear of the raw volume, op by op (the GPU's decision path). */
+static float or_trilinear_f32(const float *vol, int nx, int ny, int nz, const float *x) {
+  int n[3] = {nx, ny, nz}, i0[3], i1[3];
+  float w[3];
+  for (int a = 0; a < 3; ++a) {
+    if (n[a] == 1) { i0[a] = 0; i1[a] = 0; w[a] = 0.0f; continue; }
+    float q = x[a] * (float)n[a];
+    q = q + -0.5f;
+    q = fminf(fmaxf(q, 0.0f), (float)(n[a] - 1));
+    int i = (int)floorf(q);
+    if (i > n[a] - 2) i = n[a] - 2;
+    i0[a] = i; i1[a] = i + 1;
+    w[a] = q - (float)i;
+  }
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  float c[2][2];
+  for (int zz = 0; zz < 2; ++zz)
+    for (int yy = 0; yy < 2; ++yy) {
+      const float *row = vol + (int64_t)(zz ? i1[2] : i0[2]) * sz + (int64_t)(yy ? i1[1] : i0[1]) * sy;
+      float a0 = row[i0[0]], a1 = row[i1[0]];
+      float dlt = a1 - a0;
+      float m = w[0] * dlt;
+      c[zz][yy] = a0 + m;
+    }
+  float d0 = c[0][1] - c[0][0], m0 = w[1] * d0, e0 = c[0][0] + m0;
+  float d1 = c[1][1] - c[1][0], m1 = w[1] * d1, e1 = c[1][0] + m1;
+  float d2 = e1 - e0, m2 = w[2] * d2;
+  return e0 + m2;
+}
+
+/* FP32 transfer-function lookup, op by op: rgba of value v. */
+static void or_tf_f32(const float *lut, float v, float *rgba) {
+  float cv = fminf(fmaxf(v, 0.0f), 1.0f);
+  float u = cv * 255.0f;
+  int e = (int)floorf(u);
+  if (e > 254) e = 254;
+  float w = u - (float)e;
+  for (int c = 0; c < 4; ++c) {
+    float l0 = lut[4 * e + c], l1 = lut[4 * (e + 1) + c];
+    float dl = l1 - l0, m = w * dl;
+    rgba[c] = l0 + m;
+  }
+}
+
+/* One Woodcock flight from parameter t (Hofmann's macrocell walk): returns 1
+ * with the tentative collision parameter *tc and the majorant *mu_c of its
+ * cell, or 0 when the ray leaves [t, t1] first. */
+int or_pt_flight(const float *o, const float *d, float t, float t1, float tau, float D, const float *mumax,
+                 int ncx, int ncy, int ncz, float sx, float sy, float sz, float *tc, float *mu_c) {
+  int nc[3] = {ncx, ncy, ncz};
+  float sc[3] = {sx, sy, sz};
+  float acc = 0.0f;
+  for (int guard = 0; guard < 1 << 20; ++guard) {
+    if (!(t < t1)) return 0;
+    float tl = t + OR_PT_TINY;
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+      float m = tl * d[a];
+      float p = o[a] + m;
+      c[a] = (int)floorf(p * sc[a]);
+      if (c[a] < 0) c[a] = 0;
+      if (c[a] > nc[a] - 1) c[a] = nc[a] - 1;
+    }
+    float texit = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+      float face;
+      if (d[a] > 0.f) face = (float)(c[a] + 1) / sc[a];
+      else if (d[a] < 0.f) face = (float)c[a] / sc[a];
+      else continue;
+      float num = face - o[a];
+      texit = fminf(texit, num / d[a]);
+    }
+    texit = fminf(texit, t1);
+    float seg = texit - t;
+    if (!(seg > OR_PT_TINY)) seg = OR_PT_TINY;
+    float mu = D * mumax[((int64_t)c[2] * ncy + c[1]) * ncx + c[0]];
+    float dtau = mu * seg;
+    float next = acc + dtau;
+    if (mu > 0.0f && next >= tau) {
+      float rem = tau - acc;
+      float dt = rem / mu;
+      float tcol = t + dt;
+      *tc = fminf(tcol, t + seg);
+      *mu_c = mu;
+      return 1;
+    }
+    acc = next;
+    t = t + seg;
+  }
+  return 0;
+}
+
+static void or_pt_direction(const uint32_t *u, float *d) {
+  double z = 1.0 - 2.0 * (double)or_u01(u[0]);
+  double r = sqrt(fmax(0.0, 1.0 - z * z));
+  double phi = 6.283185307179586 * (double)or_u01(u[1]);
+  d[0] = (float)(r * cos(phi));
+  d[1] = (float)(r * sin(phi));
+  d[2] = (float)z;
+}
+
+void or_render_pt(const or_camera *cam, const float *lut, const or_pt_opts *opt, int use_net, int L, int F,
+                  int log2T, const int *res, const int *dims, int n_dims, const double *params,
+                  const float *vol, int nx, int ny, int nz, const float *mumax, int Ng,
+                  const int64_t *pix, int64_t npix, double *rgba_out) {
+  or_field f;
+  memset(&f, 0, sizeof(f));
+  f.use_net = use_net; f.L = L; f.F = F; f.log2T = log2T; f.res = res; f.dims = dims; f.n_dims = n_dims;
+  f.params = params;
+  f.weights = use_net ? params + (int64_t)L * ((int64_t)1 << log2T) * F : NULL;
+  f.vol = vol; f.nx = nx; f.ny = ny; f.nz = nz;
+  int ncx = (nx + Ng - 1) / Ng, ncy = (ny + Ng - 1) / Ng, ncz = (nz + Ng - 1) / Ng;
+  float sx = (float)nx / (float)Ng, sy = (float)ny / (float)Ng, sz = (float)nz / (float)Ng;
+  const uint32_t key[2] = {opt->seed_lo, opt->seed_hi};
+  int alen = use_net ? or_act_len(dims, n_dims) : 1;
+#pragma omp parallel
+  {
+    double *act = (double *)malloc(sizeof(double) * alen);
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t q = 0; q < npix; ++q) {
+      int64_t p = pix[q];
+      float o[3], d[3], t0, t1;
+      double Lr[3] = {0, 0, 0};
+      float hit = 0.0f;
+      or_ray(cam, (int)(p % cam->width), (int)(p / cam->width), o, d);
+      if (or_box(o, d, &t0, &t1)) {
+        float beta[3] = {1.0f, 1.0f, 1.0f};
+        uint32_t ev = 0;
+        float t = t0;
+        int bounce = 0;
+        for (;;) {
+          /* free flight of the scattering ray */
+          uint32_t ctr[4] = {(uint32_t)p, ev++, opt->frame, 0u}, u[4];
+          or_philox4x32_10(ctr, key, u);
+          float tau = (float)(-log1p(-(double)or_u01(u[0])));
+          float tc, muc;
+          if (!or_pt_flight(o, d, t, t1, tau, opt->density, mumax, ncx, ncy, ncz, sx, sy, sz, &tc, &muc)) break;
+          float x[3];
+          for (int a = 0; a < 3; ++a) { float m = tc * d[a]; x[a] = o[a] + m; }
+          float v = use_net ? (float)or_field_value(&f, x, act) : or_trilinear_f32(vol, nx, ny, nz, x);
+          float c[4];
+          or_tf_f32(lut, v, c);
+          float sig = opt->density * c[3];
+          float ratio = sig / muc;
+          if (!(or_u01(u[1]) < ratio)) { t = tc; continue; } /* null collision */
+          hit = 1.0f;
+          /* next-event estimation: a shadow ray towards the light */
+          float s0, s1;
+          int visible = 1;
+          if (or_box(x, opt->light, &s0, &s1)) {
+            float ts = s0;
+            for (;;) {
+              uint32_t c2[4] = {(uint32_t)p, ev++, opt->frame, 0u}, w2[4];
+              or_philox4x32_10(c2, key, w2);
+              float tau2 = (float)(-log1p(-(double)or_u01(w2[0])));
+              float tc2, mu2;
+              if (!or_pt_flight(x, opt->light, ts, s1, tau2, opt->density, mumax, ncx, ncy, ncz, sx, sy, sz, &tc2,
+                                &mu2))
+                break;
+              float y[3];
+              for (int a = 0; a < 3; ++a) { float m = tc2 * opt->light[a]; y[a] = x[a] + m; }
+              float v2 = use_net ? (float)or_field_value(&f, y, act) : or_trilinear_f32(vol, nx, ny, nz, y);
+              float c2v[4];
+              or_tf_f32(lut, v2, c2v);
+              float sig2 = opt->density * c2v[3];
+              float r2 = sig2 / mu2;
+              if (or_u01(w2[1]) < r2) { visible = 0; break; }
+              ts = tc2;
+            }
+          }
+          if (visible)
+            for (int ch = 0; ch < 3; ++ch) { float b = beta[ch] * c[ch]; Lr[ch] += (double)b; }
+          for (int ch = 0; ch < 3; ++ch) beta[ch] = beta[ch] * c[ch];
+          ++bounce;
+          if (bounce >= opt->max_bounces) break;
+          /* scattering: roulette and an isotropic direction */
+          uint32_t c3[4] = {(uint32_t)p, ev++, opt->frame, 0u}, w3[4];
+          or_philox4x32_10(c3, key, w3);
+          if (bounce >= 3) {
+            float qv = fminf(1.0f, fmaxf(beta[0], fmaxf(beta[1], beta[2])));
+            if (!(or_u01(w3[2]) < qv)) break;
+            for (int ch = 0; ch < 3; ++ch) beta[ch] = beta[ch] / qv;
+          }
+          for (int a = 0; a < 3; ++a) o[a] = x[a];
+          or_pt_direction(w3, d);
+          if (!or_box(o, d, &t0, &t1)) break;
+          t = t0;
+        }
+      }
+      rgba_out[4 * q + 0] = Lr[0];
+      rgba_out[4 * q + 1] = Lr[1];
+      rgba_out[4 * q + 2] = Lr[2];
+      rgba_out[4 * q + 3] = hit;
+    }
+    free(act);
+  }
+}

@@ -102,6 +102,13 @@ def lib():
         L.or_pixel_ray.argtypes = [C.POINTER(_Cam), C.c_int, C.c_int, _f32p, _f32p, _f32p]
         L.or_pixel_ray.restype = C.c_int
         L.or_box_exit.argtypes = [_f32p, _f32p]
+        L.or_pt_flight.argtypes = [_f32p, _f32p, C.c_float, C.c_float, C.c_float, C.c_float, _f32p, C.c_int,
+                                   C.c_int, C.c_int, C.c_float, C.c_float, C.c_float, C.POINTER(C.c_float),
+                                   C.POINTER(C.c_float)]
+        L.or_pt_flight.restype = C.c_int
+        L.or_render_pt.argtypes = [C.POINTER(_Cam), _f32p, C.POINTER(_PtOpts), C.c_int, C.c_int, C.c_int, C.c_int,
+                                   _i32p, _i32p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                   _f32p, C.c_int, _i64p, C.c_int64, _f64p]
         L.or_box_exit.restype = C.c_float
         L.or_mse.argtypes = [_f64p, _f64p, C.c_int64]
         L.or_mse.restype = C.c_double
@@ -365,6 +372,56 @@ def pixel_ray(cam: dict, px, py):
     t = np.zeros(2, np.float32)
     hit = lib().or_pixel_ray(C.byref(_cam(cam)), int(px), int(py), o, d, t)
     return bool(hit), o, d, t
+
+
+class _PtOpts(C.Structure):
+    _fields_ = [("density", C.c_float), ("light", C.c_float * 3), ("max_bounces", C.c_int),
+                ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("frame", C.c_uint32)]
+
+
+def _pt_opts(opts: dict) -> _PtOpts:
+    seed = int(opts.get("seed", 0))
+    return _PtOpts(float(opts["density"]), (C.c_float * 3)(*[float(v) for v in opts["light"]]),
+                   int(opts.get("max_bounces", 8)), seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF,
+                   int(opts.get("frame", 0)))
+
+
+def render_pt(cam: dict, lut, opts: dict, pixels, mumax, cell, vol=None, net: Net | None = None, params=None,
+              dims=None):
+    """Path-traced radiance (FP64) of the listed pixels for one frame: [n, 4] = RGB, hit flag.
+    mumax / cell: the macrocell majorants; vol: the raw volume (or dims (nz, ny, nx) with net)."""
+    o = _pt_opts(opts)
+    pix = np.ascontiguousarray(pixels, dtype=np.int64)
+    out = np.zeros((pix.shape[0], 4), dtype=np.float64)
+    if vol is not None:
+        vol = _f32(vol)
+        nz, ny, nx = vol.shape
+        volp = vol.ctypes.data
+    else:
+        nz, ny, nx = dims
+        volp = None
+    mu = _f32(mumax)
+    if net is not None:
+        prm = _f64(params)
+        lib().or_render_pt(C.byref(_cam(cam)), _f32(lut), C.byref(o), 1, net.L, net.F, net.log2T, net.res,
+                           net._dims(), len(net.dims), prm.ctypes.data, volp, nx, ny, nz, mu, int(cell),
+                           pix, pix.shape[0], out)
+    else:
+        z = np.zeros(1, np.int32)
+        lib().or_render_pt(C.byref(_cam(cam)), _f32(lut), C.byref(o), 0, 0, 0, 0, z, z, 0, None, volp, nx,
+                           ny, nz, mu, int(cell), pix, pix.shape[0], out)
+    return out
+
+
+def pt_flight(o, d, t, t1, tau, density, mumax, shape, cell):
+    """One Woodcock flight of the path tracer: (tentative collision t, its cell majorant) or None."""
+    nz, ny, nx = shape
+    nc = [-(-n // cell) for n in (nx, ny, nz)]
+    sc = [np.float32(n) / np.float32(cell) for n in (nx, ny, nz)]
+    tc, mc = C.c_float(0), C.c_float(0)
+    ok = lib().or_pt_flight(_f32(o), _f32(d), float(t), float(t1), float(tau), float(density), _f32(mumax),
+                            nc[0], nc[1], nc[2], float(sc[0]), float(sc[1]), float(sc[2]), C.byref(tc), C.byref(mc))
+    return (np.float32(tc.value), np.float32(mc.value)) if ok else None
 
 
 def box_exit(o, d):

@@ -568,6 +568,93 @@ def test_single_shot_shadow_empty_volume_casts_nothing():
     assert np.all(got == 0)
 
 
+def test_pt_flight_spends_the_target_optical_thickness():
+    # Hofmann's walk: the majorant's optical thickness from the start to the
+    # tentative collision equals tau; integrate it independently along the ray
+    rng = np.random.default_rng(8)
+    shape, cell = (24, 20, 28), 4
+    nc = [-(-n // cell) for n in shape]
+    mu = rng.random(nc).astype(np.float32)
+    mu[rng.random(nc) < 0.3] = 0
+    D = 5.0
+    sc = [np.float32(n) / np.float32(cell) for n in shape[::-1]]
+    n_col = 0
+    for trial in range(40):
+        o = rng.random(3).astype(np.float32) * np.float32(0.8) + np.float32(0.1)
+        d = rng.normal(size=3)
+        d = (d / np.linalg.norm(d)).astype(np.float32)
+        t1 = O.box_exit(o, d)
+        tau = np.float32(rng.exponential())
+        r = O.pt_flight(o, d, 0.0, t1, tau, D, mu, shape, cell)
+        ts = np.linspace(0.0, t1, 20001)
+        mid = (ts[:-1] + ts[1:]) / 2
+        pts = o[None, :].astype(np.float64) + mid[:, None] * d[None, :].astype(np.float64)
+        idx = [np.clip(np.floor(pts[:, a] * float(sc[a])).astype(int), 0, nc[2 - a] - 1) for a in range(3)]
+        maj = D * mu[idx[2], idx[1], idx[0]].astype(np.float64)
+        cum = np.concatenate([[0.0], np.cumsum(maj * np.diff(ts))])
+        if r is None:
+            assert cum[-1] <= tau + 0.02 * max(1.0, tau)
+            continue
+        n_col += 1
+        tc, m = r
+        assert 0 <= tc <= t1
+        got = np.interp(float(tc), ts, cum)
+        assert abs(got - tau) <= 0.02 * max(1.0, tau) + 2 * D * (t1 / 20000), (trial, got, tau)
+        # the returned majorant is the one of the collision's cell
+        pc = o.astype(np.float64) + (float(tc) - 1e-6) * d
+        cc = [int(np.clip(np.floor(pc[a] * float(sc[a])), 0, nc[2 - a] - 1)) for a in range(3)]
+        assert m == pytest.approx(D * mu[cc[2], cc[1], cc[0]], rel=1e-6)
+    assert n_col > 15
+
+
+def _pt_slab(albedo_index, D, mu_scale, frames, seed, black=False, bounces=1):
+    n = 16
+    vol = np.full((n, n, n), np.float32(albedo_index / 255.0), np.float32)
+    lut = I.ramp_lut()
+    if black:
+        lut[:, :3] = 0
+    _, mu = O.macrocells(vol, 8, lut)
+    cam = I.ortho_camera_z(32, 32)
+    out = []
+    for f in range(frames):
+        opts = dict(density=D, light=(0.0, 0.0, -1.0), max_bounces=bounces, seed=seed, frame=f)
+        out.append(O.render_pt(cam, lut, opts, np.arange(32 * 32), mu * np.float32(mu_scale), 8, vol=vol))
+    return np.concatenate(out), lut
+
+
+@pytest.mark.parametrize("mu_scale", [1.0, 3.0])
+def test_pt_single_scatter_closed_form(mu_scale):
+    # constant medium, camera rays along +z, light back along -z, one bounce:
+    # E[L] = a int_0^1 s e^{-s t} e^{-s t} dt = (a / 2)(1 - e^{-2 s}); an inflated
+    # majorant (null collisions) must not change the mean
+    k = 100
+    D = 3.0
+    img, lut = _pt_slab(k, D, mu_scale, 6, seed=11)
+    a = float(lut[k, 0])
+    sig = D * float(lut[k, 3])
+    want = 0.5 * a * (1 - np.exp(-2 * sig))
+    L = img[:, 0]
+    err = L.std() / np.sqrt(L.size)
+    assert abs(L.mean() - want) <= 4 * err, (L.mean(), want, err)
+    # P(real collision inside the box) = 1 - e^{-s}
+    hit = img[:, 3].mean()
+    assert abs(hit - (1 - np.exp(-sig))) <= 4 * np.sqrt(hit * (1 - hit) / img.shape[0])
+
+
+def test_pt_zero_albedo_is_black():
+    img, _ = _pt_slab(100, 3.0, 1.0, 1, seed=2, black=True, bounces=8)
+    assert img[:, 3].mean() > 0.5  # the medium is hit ...
+    assert np.all(img[:, :3] == 0)  # ... but nothing is scattered
+
+
+def test_pt_more_bounces_add_light():
+    one, _ = _pt_slab(200, 3.0, 1.0, 2, seed=4, bounces=1)
+    many, _ = _pt_slab(200, 3.0, 1.0, 2, seed=4, bounces=8)
+    # the first bounce is the same path in both (same random numbers until then)
+    assert np.all(many[:, 0] >= one[:, 0] - 1e-12)
+    assert many[:, 0].mean() > 1.05 * one[:, 0].mean()
+
+
 def test_ortho_rays_through_pixel_centres():
     cam = I.ortho_camera_z(64, 64)
     for px, py in [(0, 0), (17, 40), (63, 63)]:
