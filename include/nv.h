@@ -286,6 +286,31 @@ nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_
  * number of evaluated samples.  Asynchronous on the network's stream. */
 nv_status nv_render_inshader(nv_ctx *net, const nv_camera *cam, const float *lut_dev, const nv_macrocells *mc,
                              const nv_render_opts *opts, float *rgba_dev, int64_t *samples_dev);
+/* Volumetric path tracing with sample streaming (Sec. 5.2.2, Alg. 1, Eq. 1-2):
+ * one path per pixel and call.  Extinction sigma(x) = density * LUT opacity
+ * per unit length, single-scattering albedo = LUT colour, isotropic phase, a
+ * directional light towards `light` (its irradiance cancels the phase
+ * factor), black background.  Free flights are Woodcock tracking against the
+ * majorant density * mu_max of each macrocell of `mc` (required), walked
+ * cell by cell (Hofmann): tau = -log(1 - zeta) is spent along the ray and
+ * the tentative collision accepted with probability sigma / majorant.  Every
+ * real collision sends a shadow ray towards the light, tracked the same way
+ * (the light counts when it leaves the volume unblocked), then throughput *=
+ * albedo, Russian roulette from the third bounce and an isotropic direction;
+ * a path ends on leaving the volume or after max_bounces real collisions.
+ * Random numbers: Philox4x32-10, key = seed, counter = (pixel, event, frame,
+ * 0); per frame the caller averages the images.  rgba_dev: RGB radiance and
+ * A = 1 where the camera ray's path had a real collision.  Network values
+ * come from `net` (NULL: the raw volume `raw`). */
+typedef struct {
+  float density;    /* D: extinction per unit length at LUT opacity 1 */
+  float light[3];   /* unit direction towards the directional light */
+  int max_bounces;  /* real collisions per path, >= 1 */
+  uint64_t seed;
+  uint32_t frame;
+} nv_pt_opts;
+nv_status nv_render_pt(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
+                       const float *lut_dev, const nv_macrocells *mc, const nv_pt_opts *opts, float *rgba_dev);
 /* Iterations and samples of the last nv_render (synchronises). */
 nv_status nv_render_stats(nv_renderer *r, int *iterations, int64_t *samples);
 

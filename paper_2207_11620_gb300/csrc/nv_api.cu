@@ -448,6 +448,9 @@ static void renderer_free(nv_renderer *r) {
   cudaFree(r->seg_exp);
   cudaFree(r->aux[0]);
   cudaFree(r->aux[1]);
+  cudaFree(r->pt[0]);
+  cudaFree(r->pt[1]);
+  cudaFree(r->pt_coords);
   cudaFree(r->nvalid);
   cudaFree(r->counters);
   cudaFree(r->d_samples);
@@ -538,6 +541,24 @@ extern "C" nv_status nv_render_inshader(nv_ctx *net, const nv_camera *cam, const
     return nv_fail(NV_ERR_UNSUPPORTED, "nv_render_inshader: emission-absorption with the fixed step only");
   if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render_inshader: tan_half_fovy < 0");
   return render_inshader(net, *cam, lut, mc, *opts, rgba, reinterpret_cast<unsigned long long *>(samples_dev));
+}
+
+extern "C" nv_status nv_render_pt(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
+                                  const float *lut, const nv_macrocells *mc, const nv_pt_opts *opts, float *rgba) {
+  if (!r || !cam || !lut || !mc || !opts || !rgba) return nv_fail(NV_ERR_ARG, "nv_render_pt: NULL argument");
+  if (!net) NV_TRY(check_volume(raw, "nv_render_pt"));
+  if (net && !net->params_set) return nv_fail(NV_ERR_STATE, "nv_render_pt: network parameters never set");
+  if (cam->width < 1 || cam->height < 1) return nv_fail(NV_ERR_ARG, "nv_render_pt: image %dx%d", cam->width, cam->height);
+  if ((int64_t)cam->width * cam->height > r->max_pixels)
+    return nv_fail(NV_ERR_ARG, "nv_render_pt: %dx%d exceeds the renderer's %lld pixels", cam->width, cam->height,
+                   (long long)r->max_pixels);
+  if (!mc->mu_max_dev || mc->cell < 1 || mc->nx < 1 || mc->ny < 1 || mc->nz < 1)
+    return nv_fail(NV_ERR_ARG, "nv_render_pt: bad macrocell grid");
+  const float l2 = opts->light[0] * opts->light[0] + opts->light[1] * opts->light[1] + opts->light[2] * opts->light[2];
+  if (!(opts->density > 0.f) || !(fabsf(l2 - 1.f) < 1e-3f) || opts->max_bounces < 1)
+    return nv_fail(NV_ERR_ARG, "nv_render_pt: density > 0, a unit light direction and max_bounces >= 1");
+  if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render_pt: tan_half_fovy < 0");
+  return render_pt_impl(r, net, raw, *cam, lut, *mc, *opts, rgba);
 }
 
 extern "C" nv_status nv_render_stats(nv_renderer *r, int *iterations, int64_t *samples) {

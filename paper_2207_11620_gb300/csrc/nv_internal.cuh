@@ -76,6 +76,8 @@ struct nv_renderer {
   float *values;       // [max_pixels*K] sample values
   float *seg_exp;      // [max_pixels*K] opacity exponents of adaptive-step samples (NULL: fixed step only)
   float *aux[2];       // [5][max_pixels] single-shot shadow state, ping-pong with ray (NULL: no shadows)
+  float *pt[2];        // path-tracer state [28][max_pixels], ping-pong (allocated on first use)
+  float *pt_coords;    // second buffer of pending collision points [max_pixels][3]
   int *nvalid;         // [max_pixels] valid samples of each ray this iteration
   int *counters;       // device: [0] live count (current), [1] live count (next)
   int *h_count;        // pinned host mirror of the live count
@@ -282,6 +284,9 @@ nv_status launch_mc_update(const float *xyz, const float *val, int64_t n, const 
                            uint32_t step, int nx, int ny, int nz, int cell, float *minmax, cudaStream_t s);
 nv_status launch_mc_mu(const float *minmax, int nx, int ny, int nz, int cell, const float *lut, float *mu,
                        cudaStream_t s);
+// Path tracing with sample streaming (k_pt.cu); mc supplies the majorants.
+nv_status render_pt_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera &cam, const float *lut,
+                         const nv_macrocells &mc, const nv_pt_opts &o, float *rgba);
 // In-shader ray march (k_inshader.cu); samples (nullable, device) counts the
 // evaluated samples.
 nv_status render_inshader(nv_ctx *c, const nv_camera &cam, const float *lut, const nv_macrocells *mc,

@@ -52,6 +52,11 @@ def render_opts(opts: dict, K: int) -> RenderOpts:
                       float(opts.get("ambient", 0.0)))
 
 
+class PtOpts(C.Structure):
+    _fields_ = [("density", C.c_float), ("light", C.c_float * 3), ("max_bounces", C.c_int),
+                ("seed", C.c_uint64), ("frame", C.c_uint32)]
+
+
 class Macrocells(C.Structure):
     _fields_ = [("mu_max_dev", C.c_void_p), ("cell", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
                 ("nz", C.c_int)]
@@ -75,6 +80,8 @@ EXPORTS = {
     "nv_set_adam": ([C.c_void_p, C.POINTER(AdamCfg)], C.c_int),
     "nv_set_loss_scale": ([C.c_void_p, C.c_float], C.c_int),
     "nv_set_loss": ([C.c_void_p, C.c_int], C.c_int),
+    "nv_render_pt": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                      C.c_void_p], C.c_int),
     "nv_macrocells_reset": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p], C.c_int),
     "nv_macrocells_update": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                               C.c_void_p], C.c_int),
@@ -405,6 +412,22 @@ class Renderer:
             mp = C.byref(m)
         _check(lib().nv_render(self._h, net.handle if net is not None else None, vp, C.byref(c),
                                _dev(lut, name="lut"), mp, C.byref(o), _dev(out, name="out")))
+        return out
+
+    def render_pt(self, cam: dict, lut, opts: dict, mc: tuple, net: NeuralVolume | None = None, raw=None,
+                  out=None):
+        """One path-traced frame (nv_render_pt): RGB radiance + hit flag [H, W, 4].
+        opts: density, light (unit direction to it), max_bounces (8), seed, frame."""
+        c = camera(cam)
+        if out is None:
+            out = torch.empty((c.height, c.width, 4), dtype=torch.float32, device="cuda")
+        o = PtOpts(float(opts["density"]), (C.c_float * 3)(*[float(v) for v in opts["light"]]),
+                   int(opts.get("max_bounces", 8)), int(opts.get("seed", 0)), int(opts.get("frame", 0)))
+        mu, cell, shape = mc
+        m = Macrocells(_dev(mu, name="mu_max").value, int(cell), int(shape[2]), int(shape[1]), int(shape[0]))
+        vp = C.byref(volume(raw)) if raw is not None else None
+        _check(lib().nv_render_pt(self._h, net.handle if net is not None else None, vp, C.byref(c),
+                                  _dev(lut, name="lut"), C.byref(m), C.byref(o), _dev(out, name="out")))
         return out
 
     def stats(self):
