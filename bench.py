@@ -459,6 +459,9 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
     raw = raw.clone()
     it, ns = r.stats()
     out = {"image": [W, H], "raw_ms": raw_ms, "raw_samples_per_frame": ns, "raw_iterations": it}
+    _, raw_pt_ms = _median_frame_ms(torch, frames, lambda: r.render_pt(
+        cam, lut, dict(density=float(D), light=(0.0, 0.8, -0.6), max_bounces=8, seed=3), mc, raw=vt))
+    out["raw_path_tracing_1spp_ms"] = raw_pt_ms
     steps = train_steps or cfg["train_steps"]
     for prec in ("fp16", "bf16"):
         net = nv.NeuralVolume(prec=prec, **c.kwargs())
@@ -483,6 +486,16 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
         ad_img, ad_ms = _time_render(r, torch, frames, cam=cam, lut=lut, opts=ad_opts, net=net, mc=mc)
         ad_it, ad_ns = r.stats()
         ad_psnr = _psnr(nv.image_mse(ad_img, raw).item())
+        # single-shot heuristic shadows and path tracing (Sec. 5.2.2) of the same network
+        light = (0.0, 0.8, -0.6)
+        sh_img, sh_ms = _time_render(r, torch, frames, cam=cam, lut=lut,
+                                     opts=dict(opts, shade=1, light=light, ambient=0.25), net=net, mc=mc)
+        sh_it, sh_ns = r.stats()
+        pt_opts = dict(density=float(D), light=light, max_bounces=8, seed=3)
+        _, pt_ms = _median_frame_ms(torch, frames, lambda: r.render_pt(cam, lut, pt_opts, mc, net=net))
+        pt_it, pt_ns = r.stats()
+        out_pt = {"frame_ms": pt_ms, "tentative_collisions_per_frame": pt_ns, "iterations": pt_it,
+                  "network_samples_per_s": pt_ns / (pt_ms / 1e3), "density": float(D), "max_bounces": 8}
         out[prec] = {"train_steps": steps, "train_ms_per_step": e0.elapsed_time(e1) / steps,
                      "frame_ms": ms, "samples_per_frame": ns, "iterations": it,
                      "decoded_samples_per_s": ns / (ms / 1e3), "image_psnr_db": _psnr(mse),
@@ -491,7 +504,9 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
                                   "max_abs_diff_vs_streaming": float((is_img - img).abs().max().item()),
                                   "streaming_speedup": is_ms / ms},
                      "adaptive_step": {"step_max_voxels": cfg["step_voxels"] * 2 * cfg["cell"], "frame_ms": ad_ms,
-                                       "samples_per_frame": ad_ns, "iterations": ad_it, "image_psnr_db": ad_psnr}}
+                                       "samples_per_frame": ad_ns, "iterations": ad_it, "image_psnr_db": ad_psnr},
+                     "single_shot_shadows": {"frame_ms": sh_ms, "samples_per_frame": sh_ns, "iterations": sh_it},
+                     "path_tracing_1spp": out_pt}
         net.close()
     r.close()
     del vt
