@@ -105,33 +105,18 @@ class Clocks:
 
 
 def dist_setup(n_gpus):
-    import torch
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
-    return ws, rank, local
+    from paper_2207_11620_gb300 import replicas
+    return replicas.setup()
 
 
 def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2207_11620_gb300 import replicas
+    replicas.barrier(ws)
 
 
 def max_over_ranks(ws, v):
-    if ws == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2207_11620_gb300 import replicas
+    return replicas.max_over_ranks(ws, v)
 
 
 # ------------------------------------------------------------------- oracle ---
@@ -320,7 +305,8 @@ def run_ours(args):
     k_adam = net.profile_read("adam")
     k_fin = net.profile_read("finish")
     ms_max = max_over_ranks(ws, ms)
-    value = ws * batch * args.steps / (ms_max / 1e3)
+    from paper_2207_11620_gb300 import replicas
+    value = replicas.job_throughput(ws, batch * args.steps, ms_max / 1e3)
 
     # end to end through the C ABI: batches from pinned host memory, loss read back
     n_e2e = 4
@@ -346,7 +332,7 @@ def run_ours(args):
     barrier(ws)
     e2e_ms = max(e0.elapsed_time(e1), 1e3 * t_wall)
     e2e_ms = max_over_ranks(ws, e2e_ms)
-    e2e_value = ws * batch * args.steps / (e2e_ms / 1e3)
+    e2e_value = replicas.job_throughput(ws, batch * args.steps, e2e_ms / 1e3)
     clk = clocks.stop()
     # fresh-run sanity: the loss stays finite
     assert np.isfinite(loss_host.item())
