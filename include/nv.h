@@ -134,7 +134,10 @@ nv_status nv_info(const nv_ctx *ctx, int64_t *n_params, int64_t *n_table, int *l
  * refreshes the FP16/BF16 shadow copy used by the tensor-core kernels. */
 nv_status nv_set_params(nv_ctx *ctx, const float *params_any);
 nv_status nv_get_params(nv_ctx *ctx, float *params_any);
-/* Device pointer and length of an internal FP32 buffer (nv_buffer); owned by the context. */
+/* Device pointer and length of an internal FP32 buffer (nv_buffer); owned by the context.
+ * Writes through the params pointer do not reach the FP16/BF16 shadow (Adam
+ * rewrites the shadow only of the parameters it changes): set parameters with
+ * nv_set_params. */
 nv_status nv_buffer_ptr(nv_ctx *ctx, int which, float **ptr_dev, int64_t *n);
 /* Adam hyper-parameters (App. B lists beta 0.9 / 0.999, eps 1e-15). */
 nv_status nv_set_adam(nv_ctx *ctx, const nv_adam_cfg *cfg);

@@ -3,7 +3,8 @@
 // Per parameter the kernel reads p, g, m, v (16 B) and writes p, m, v, g = 0
 // (16 B) plus the FP16/BF16 shadow (2 B) in tensor-core precisions: 32-34 B of
 // algorithmic traffic per parameter, float4-vectorised, grid-stride over a
-// grid of a few CTAs per SM.  The step counter, the overflow flag and the loss
+// grid of a few CTAs per SM.  Groups of four parameters that no gradient has
+// reached yet (zero g, m and v) are read but not rewritten.  The step counter, the overflow flag and the loss
 // scale live on the device, so a step whose gradient overflowed is skipped
 // without a host round trip (the gradient is still cleared).
 #include <algorithm>
@@ -94,7 +95,14 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__re
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int64_t i = base + u * nthr;
-      if (i < n4) {
+      // four parameters with zero gradient and zero moments (never reached by
+      // a gradient: hash slots no point has touched) leave Adam unchanged bit
+      // for bit when there is no L2 term; their stores are skipped
+      const bool idle = hp.l2 == 0.f && (gg[u].x == 0.f) & (gg[u].y == 0.f) & (gg[u].z == 0.f) &
+                                              (gg[u].w == 0.f) & (mm[u].x == 0.f) & (mm[u].y == 0.f) &
+                                              (mm[u].z == 0.f) & (mm[u].w == 0.f) & (vv[u].x == 0.f) &
+                                              (vv[u].y == 0.f) & (vv[u].z == 0.f) & (vv[u].w == 0.f);
+      if (i < n4 && !idle) {
         upd(pp[u].x, gg[u].x, mm[u].x, vv[u].x);
         upd(pp[u].y, gg[u].y, mm[u].y, vv[u].y);
         upd(pp[u].z, gg[u].z, mm[u].z, vv[u].z);
