@@ -366,11 +366,11 @@ nv_status nv_volume_mse(nv_ctx *ctx, const nv_volume *vol, double *mse_dev);
 typedef enum {
   NV_K_MLP = 0,     /* the MLP kernel (FP32 path: the whole fused encode + MLP + scatter kernel) */
   NV_K_ADAM = 1,
-  NV_K_FINISH = 2,
+  NV_K_FINISH = 2,  /* no launches: the step's book-keeping runs in the last CTA of Adam */
   NV_K_RENDER = 3,
   NV_K_OTHER = 4,
   NV_K_ENCODE = 5,  /* tensor-core path: hash gather into feature tiles */
-  NV_K_SCATTER = 6  /* tensor-core path: input gradient into the table gradient */
+  NV_K_SCATTER = 6  /* no launches: the tensor-core path scatters inside the MLP kernel */
 } nv_kclass;
 nv_status nv_profile_enable(nv_ctx *ctx, int enable);
 nv_status nv_profile_read(nv_ctx *ctx, int kclass, double *total_ms, int *launches);

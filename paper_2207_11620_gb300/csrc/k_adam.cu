@@ -6,7 +6,8 @@
 // grid of a few CTAs per SM.  Groups of four parameters that no gradient has
 // reached yet (zero g, m and v) are read but not rewritten.  The step counter, the overflow flag and the loss
 // scale live on the device, so a step whose gradient overflowed is skipped
-// without a host round trip (the gradient is still cleared).
+// without a host round trip (the gradient is still cleared); the last CTA of
+// the launch does the step's book-keeping.
 #include <algorithm>
 
 #include "nv_internal.cuh"
@@ -38,11 +39,25 @@ __device__ __forceinline__ void put_shadow(void *shadow, int64_t i, float4 pp) {
   }
 }
 
+// Book-keeping after the update, by the last CTA to finish: count the step or,
+// after an overflow, halve the loss scale; publish the batch loss.
+__device__ __forceinline__ void step_finish(DevState *ds, double inv_n, double *loss_out) {
+  if (ds->overflow) {
+    ds->loss_scale *= 0.5f;
+    ds->overflow = 0;
+  } else {
+    ds->step += 1;
+  }
+  ds->loss_mean = ds->loss_acc * inv_n;
+  ds->loss_acc = 0.0;
+  if (loss_out) *loss_out = ds->loss_mean;
+}
+
 template <int SHADOW>  // 0 none, 1 fp16, 2 bf16
 __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__restrict__ g,
                                               float *__restrict__ m, float *__restrict__ v,
-                                              void *__restrict__ shadow, int64_t n, AdamHP hp,
-                                              const DevState *__restrict__ ds) {
+                                              void *__restrict__ shadow, int64_t n, AdamHP hp, DevState *ds,
+                                              double inv_n, double *loss_out) {
   // bias corrections of step t (Kingma & Ba) and the decayed learning rate of
   // step index t - 1 (App. B): one FP64 evaluation per CTA
   __shared__ float s_bc[3];
@@ -77,10 +92,9 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__re
   if (skip) {  // an overflowed step: only clear the gradient
     for (int64_t i = t0; i < n4; i += nthr) go[i] = zero;
     for (int64_t i = (n4 << 2) + t0; i < n; i += nthr) g[i] = 0.f;
-    return;
   }
   // kU float4 of each of p, g, m, v are loaded before anything is stored
-  for (int64_t base = t0; base < n4; base += nthr * kU) {
+  for (int64_t base = skip ? n4 : t0; base < n4; base += nthr * kU) {
     float4 gg[kU], pp[kU], mm[kU], vv[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -116,7 +130,7 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__re
     }
   }
   // tail (n not a multiple of 4)
-  for (int64_t i = (n4 << 2) + t0; i < n; i += nthr) {
+  for (int64_t i = (n4 << 2) + t0; i < n && !skip; i += nthr) {
     float gg = g[i];
     g[i] = 0.f;
     float pp = p[i], mm = m[i], vv = v[i];
@@ -127,20 +141,17 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ p, float *__re
     if (SHADOW == 1) reinterpret_cast<__half *>(shadow)[i] = __float2half_rn(pp);
     else if (SHADOW == 2) reinterpret_cast<__nv_bfloat16 *>(shadow)[i] = __float2bfloat16_rn(pp);
   }
-}
-
-// Book-keeping after the update: count the step or, after an overflow, halve
-// the loss scale; publish the batch loss.
-__global__ void k_step_finish(DevState *ds, double inv_n, double *loss_out) {
-  if (ds->overflow) {
-    ds->loss_scale *= 0.5f;
-    ds->overflow = 0;
-  } else {
-    ds->step += 1;
+  // every CTA has read step and overflow above; the last one to get here
+  // updates them for the next step
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ds->adam_done, 1u) == gridDim.x - 1) {
+      __threadfence();
+      step_finish(ds, inv_n, loss_out);
+      ds->adam_done = 0;
+    }
   }
-  ds->loss_mean = ds->loss_acc * inv_n;
-  ds->loss_acc = 0.0;
-  if (loss_out) *loss_out = ds->loss_mean;
 }
 
 template <int SHADOW>
@@ -153,7 +164,7 @@ __global__ void k_shadow(const float *__restrict__ p, void *__restrict__ shadow,
 
 }  // namespace
 
-nv_status launch_adam(nv_ctx *c) {
+nv_status launch_adam(nv_ctx *c, double inv_n, double *loss_out) {
   AdamHP hp{c->adam.lr,          c->adam.beta1,          c->adam.beta2,     c->adam.eps,
             c->adam.l2_reg,      c->adam.decay_start,    c->adam.decay_interval, c->adam.decay_base};
   int64_t n = c->n_params;
@@ -168,22 +179,17 @@ nv_status launch_adam(nv_ctx *c) {
   switch (c->prec) {
     case NV_FP16:
       k_adam<1><<<(unsigned)grid, 256, 0, c->stream>>>(c->params, c->grads, c->adam_m, c->adam_v, c->shadow, n,
-                                                        hp, c->ds);
+                                                        hp, c->ds, inv_n, loss_out);
       break;
     case NV_BF16:
       k_adam<2><<<(unsigned)grid, 256, 0, c->stream>>>(c->params, c->grads, c->adam_m, c->adam_v, c->shadow, n,
-                                                        hp, c->ds);
+                                                        hp, c->ds, inv_n, loss_out);
       break;
     default:
       k_adam<0><<<(unsigned)grid, 256, 0, c->stream>>>(c->params, c->grads, c->adam_m, c->adam_v, nullptr, n, hp,
-                                                        c->ds);
+                                                        c->ds, inv_n, loss_out);
   }
   return nv_cuda_check(cudaGetLastError(), "k_adam launch");
-}
-
-nv_status launch_step_finish(nv_ctx *c, double inv_n, double *loss_out) {
-  k_step_finish<<<1, 1, 0, c->stream>>>(c->ds, inv_n, loss_out);
-  return nv_cuda_check(cudaGetLastError(), "k_step_finish launch");
 }
 
 nv_status launch_shadow(nv_ctx *c) {

@@ -314,11 +314,8 @@ extern "C" nv_status nv_backward(nv_ctx *c, const float *xyz, int64_t n, const f
 extern "C" nv_status nv_optimizer_step(nv_ctx *c) {
   if (!c) return nv_fail(NV_ERR_ARG, "nv_optimizer_step: ctx is NULL");
   int tk = prof_begin(c);
-  NV_TRY(launch_adam(c));
+  NV_TRY(launch_adam(c, 0.0, nullptr));
   prof_end(c, NV_K_ADAM, tk);
-  tk = prof_begin(c);
-  NV_TRY(launch_step_finish(c, 0.0, nullptr));
-  prof_end(c, NV_K_FINISH, tk);
   return NV_OK;
 }
 
@@ -385,11 +382,8 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
     prof_end(c, NV_K_OTHER, tk1);
   }
   int tk = prof_begin(c);
-  NV_TRY(launch_adam(c));
+  NV_TRY(launch_adam(c, 1.0 / (double)n, loss_dev));
   prof_end(c, NV_K_ADAM, tk);
-  tk = prof_begin(c);
-  NV_TRY(launch_step_finish(c, 1.0 / (double)n, loss_dev));
-  prof_end(c, NV_K_FINISH, tk);
   return NV_OK;
 }
 

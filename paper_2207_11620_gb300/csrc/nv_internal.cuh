@@ -34,6 +34,7 @@ struct DevState {
   int overflow;       // set when a gradient contribution was not finite
   float loss_scale;   // static loss scale of the tensor-core backward
   int err;            // set by a kernel whose bounded wait ran out
+  unsigned adam_done; // CTAs of the running Adam launch that have finished (the last one resets it)
 };
 
 struct nv_ctx {
@@ -265,8 +266,9 @@ nv_status launch_mlp_tc_ext(const nv_ctx *c, int mode, const MlpArgs &a, const i
                             int64_t n_upper, double *acc);
 bool tc_supported(const NetDesc &nd);
 // optimizer
-nv_status launch_adam(nv_ctx *c);
-nv_status launch_step_finish(nv_ctx *c, double inv_n, double *loss_out);
+// Adam over all parameters; its last CTA counts the step (or halves the loss
+// scale after an overflow) and publishes loss_acc * inv_n into loss_out.
+nv_status launch_adam(nv_ctx *c, double inv_n, double *loss_out);
 nv_status launch_scale_double(double *x, double s, cudaStream_t st);
 nv_status launch_shadow(nv_ctx *c);
 // sampling, macrocells, rendering, reductions
