@@ -36,8 +36,12 @@ __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t
   const float3 x = point_at(ps, cs.off + q);
   if (tgt && c == 0) tgt[q] = nv_trilinear(ps.vol.data_dev, ps.vol.nx, ps.vol.ny, ps.vol.nz, x.x, x.y, x.z);
   float f8[8];
-  if constexpr (F == 2) gather_levels_f2<BF, 4>(shadow, nd, c * 4, x.x, x.y, x.z, f8);
-  else gather_levels<F, BF, 8 / F>(shadow, nd, c * (8 / F), x.x, x.y, x.z, f8);
+  if constexpr (F == 2) {
+    gather_levels_f2<BF, 4>(shadow, nd, c * 4, x.x, x.y, x.z, f8);
+  } else {  // one level at a time: fewer registers, more resident warps
+#pragma unroll
+    for (int g = 0; g < 8 / F; ++g) gather_levels<F, BF, 1>(shadow, nd, c * (8 / F) + g, x.x, x.y, x.z, f8 + g * F);
+  }
   uint4 u;
   u.x = pack16x2<BF>(f8[0], f8[1]);
   u.y = pack16x2<BF>(f8[2], f8[3]);
