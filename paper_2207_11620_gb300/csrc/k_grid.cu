@@ -19,7 +19,7 @@ namespace {
 template <int F, bool BF>
 __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t *__restrict__ shadow, PointSrc ps,
                                                       ChunkSpan cs, uint8_t *__restrict__ feat,
-                                                      float *__restrict__ tgt) {
+                                                      float *__restrict__ tgt, float *__restrict__ xyz_out) {
   const int D0 = nd.dims[0];
   const int C = D0 / 8;
   const int64_t n = chunk_count(cs);
@@ -34,7 +34,14 @@ __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t
     return;
   }
   const float3 x = point_at(ps, cs.off + q);
-  if (tgt && c == 0) tgt[q] = nv_trilinear(ps.vol.data_dev, ps.vol.nx, ps.vol.ny, ps.vol.nz, x.x, x.y, x.z);
+  if (c == 0) {
+    if (tgt) tgt[q] = nv_trilinear(ps.vol.data_dev, ps.vol.nx, ps.vol.ny, ps.vol.nz, x.x, x.y, x.z);
+    if (xyz_out) {
+      xyz_out[3 * q] = x.x;
+      xyz_out[3 * q + 1] = x.y;
+      xyz_out[3 * q + 2] = x.z;
+    }
+  }
   float f8[8];
   if constexpr (F == 2) {
     gather_levels_f2<BF, 4>(shadow, nd, c * 4, x.x, x.y, x.z, f8);
@@ -54,9 +61,10 @@ inline unsigned grid_for(int64_t items) { return (unsigned)((items + 255) / 256)
 
 }  // namespace
 
-// tgt (nullable): [cap] targets of a Philox training sample (ps.kind == 2).
+// tgt (nullable): [cap] targets of a Philox training sample (ps.kind == 2);
+// xyz_out (nullable): [cap][3] its points, for the MLP kernel's scatter.
 nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat,
-                              float *tgt) {
+                              float *tgt, float *xyz_out) {
   const int C = c->nd.dims[0] / 8;
   const int64_t npad = (cs.cap + 127) & ~int64_t(127);
   if (npad == 0) return NV_OK;
@@ -65,12 +73,12 @@ nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSp
   const bool bf = c->prec == NV_BF16;
   switch (c->nd.F) {
     case 2:
-      if (bf) k_encode_tiles<2, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt);
-      else k_encode_tiles<2, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt);
+      if (bf) k_encode_tiles<2, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out);
+      else k_encode_tiles<2, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out);
       break;
     case 4:
-      if (bf) k_encode_tiles<4, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt);
-      else k_encode_tiles<4, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt);
+      if (bf) k_encode_tiles<4, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out);
+      else k_encode_tiles<4, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out);
       break;
     default:
       return nv_fail(NV_ERR_UNSUPPORTED, "tensor-core encode: F=%d", c->nd.F);

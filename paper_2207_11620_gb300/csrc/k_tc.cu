@@ -34,7 +34,7 @@
 #include "tc_ptx.cuh"
 
 nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat,
-                              float *tgt);
+                              float *tgt, float *xyz_out);
 
 namespace {
 
@@ -571,18 +571,21 @@ bool tc_supported(const NetDesc &nd) {
 }
 
 // Scratch of the tensor-core path: one chunk of features (16-bit, tile layout)
-// and of sampled training targets (FP32), allocated on first use.
+// and of sampled training points and targets (FP32), allocated on first use.
 static nv_status tc_scratch(nv_ctx *c, int64_t points) {
   const int64_t cap = points < kChunk ? ((points + kTP - 1) / kTP) * kTP : kChunk;
   if (c->tc_cap >= cap) return NV_OK;
   cudaFree(c->tc_feat);
   cudaFree(c->tc_tgt);
+  cudaFree(c->tc_xyz);
   c->tc_feat = nullptr;
   c->tc_tgt = nullptr;
+  c->tc_xyz = nullptr;
   c->tc_cap = 0;
   const int D0 = c->nd.dims[0];
   cudaError_t e = cudaMalloc(&c->tc_feat, (size_t)cap * D0 * 2);
   if (e == cudaSuccess) e = cudaMalloc(&c->tc_tgt, (size_t)cap * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->tc_xyz, (size_t)cap * 12);
   if (e != cudaSuccess) return nv_cuda_check(e, "tensor-core scratch");
   c->tc_cap = cap;
   return NV_OK;
@@ -608,16 +611,26 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
     ps.seed = a.seed;
     ps.step = a.sample_step;
   }
-  float *tgt = (mode == MODE_TRAIN && ps.kind == 2) ? c->tc_tgt : nullptr;
+  // a sampled training batch: the gather kernel computes each Philox point
+  // once for the MLP kernel too (its points and targets)
+  const bool sampled = mode == MODE_TRAIN && ps.kind == 2;
+  float *tgt = sampled ? c->tc_tgt : nullptr;
+  float *xyz_out = sampled ? c->tc_xyz : nullptr;
   for (int64_t off = 0; off < n_upper; off += c->tc_cap) {
     ChunkSpan cs{n_dev, n_mult, a.n, off, n_upper - off < c->tc_cap ? n_upper - off : c->tc_cap};
     int tk = prof_begin(c);
-    s = launch_encode_tiles(c, ps, cs, c->tc_feat, tgt);
+    s = launch_encode_tiles(c, ps, cs, c->tc_feat, tgt, xyz_out);
     prof_end(c, NV_K_ENCODE, tk);
     if (s != NV_OK) return s;
     tk = prof_begin(c);
-    s = c->prec == NV_BF16 ? dispatch_shape<true>(c, mode, a, ps, cs, c->tc_feat, tgt, acc)
-                           : dispatch_shape<false>(c, mode, a, ps, cs, c->tc_feat, tgt, acc);
+    PointSrc pm = ps;
+    if (sampled) {
+      pm.kind = 0;
+      pm.xyz = c->tc_xyz;
+      pm.xyz_off = off;
+    }
+    s = c->prec == NV_BF16 ? dispatch_shape<true>(c, mode, a, pm, cs, c->tc_feat, tgt, acc)
+                           : dispatch_shape<false>(c, mode, a, pm, cs, c->tc_feat, tgt, acc);
     prof_end(c, NV_K_MLP, tk);
     if (s != NV_OK) return s;
   }

@@ -87,6 +87,7 @@ static void ctx_free(nv_ctx *c) {
   cudaFree(c->batch);
   cudaFree(c->tc_feat);
   cudaFree(c->tc_tgt);
+  cudaFree(c->tc_xyz);
   delete c;
 }
 

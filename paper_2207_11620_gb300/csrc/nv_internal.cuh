@@ -59,6 +59,7 @@ struct nv_ctx {
   struct Prof *prof;                        // kernel timing (nv_profile_enable), NULL when off
   uint8_t *tc_feat;                         // tensor-core path: one chunk of 16-bit features (tile layout)
   float *tc_tgt;                            // tensor-core path: one chunk of sampled training targets
+  float *tc_xyz;                            // tensor-core path: the points of that chunk [cap][3]
   int64_t tc_cap;                           // points per chunk of the two above
 };
 

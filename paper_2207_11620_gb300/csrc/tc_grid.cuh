@@ -9,7 +9,8 @@
 
 // Where the points of a launch come from.
 struct PointSrc {
-  const float *xyz;   // kind 0: [n][3]
+  const float *xyz;   // kind 0: [n][3] (point p at row p - xyz_off)
+  int64_t xyz_off;
   int kind;           // 0: xyz array, 1: voxel centres of vol, 2: Philox training sample
   nv_volume vol;      // kind 1 and the training target of kind 2
   uint64_t seed;      // kind 2
@@ -17,7 +18,10 @@ struct PointSrc {
 };
 
 __device__ __forceinline__ float3 point_at(const PointSrc &s, int64_t p) {
-  if (s.kind == 0) return make_float3(s.xyz[3 * p], s.xyz[3 * p + 1], s.xyz[3 * p + 2]);
+  if (s.kind == 0) {
+    const float *r = s.xyz + 3 * (p - s.xyz_off);
+    return make_float3(r[0], r[1], r[2]);
+  }
   if (s.kind == 1) {
     const int64_t nx = s.vol.nx, ny = s.vol.ny;
     const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / (nx * ny));
