@@ -193,7 +193,36 @@ def ncu_traffic(kernel):
     return None
 
 
-def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d, L, F):
+def l2_peaks(nv, torch):
+    """Measured rates (accesses/s) of scattered 16-byte FP32 vector reductions into a 64 MiB buffer and of
+    scattered 16-byte loads from a 32 MiB buffer -- the L2-resident sizes of config 2's FP32 table gradient
+    and 16-bit tables -- by the library's measurement kernels; median of 5 launches of 2^26 accesses."""
+    ops = 1 << 26
+    red_buf = torch.zeros((1 << 22, 4), dtype=torch.float32, device="cuda")
+    ld_buf = torch.ones((1 << 21, 4), dtype=torch.float32, device="cuda")
+    sink = torch.zeros(1024, dtype=torch.int32, device="cuda")
+
+    def rate(fn):
+        fn(0)
+        torch.cuda.synchronize()
+        ts = []
+        for s in range(1, 6):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(s)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ops / (statistics.median(ts) / 1e3)
+    red = rate(lambda s: nv.peak_scatter(red_buf, ops, seed=s))
+    ld = rate(lambda s: nv.peak_gather(ld_buf, ops, sink, seed=s))
+    del red_buf, ld_buf
+    return {"scatter_reductions_per_s": red, "gather_loads_per_s": ld,
+            "how": "2^26 scattered 16-byte FP32 vector reductions into 64 MiB / 16-byte loads from 32 MiB, "
+                   "median of 5 launches (nv_peak_scatter / nv_peak_gather)"}
+
+
+def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d, L, F, l2pk=None):
     """Roofline of one kernel of the config-2 step from its live average launch time.
 
     Algorithmic bytes / FLOPs per launch (per unit x units):
@@ -227,6 +256,12 @@ def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d, L, F)
         if kind == "encode":
             r["limiter"] = ("L1-to-L2 request rate of the scattered 32-byte sector gathers; coarse levels hit "
                             "in L1 and the 16-bit tables in L2, so DRAM carries a fraction of these bytes")
+            if l2pk:  # 16-byte group loads: 5 per point and level at F = 2, 6 at F = 4, + 8 target voxels
+                loads = batch * (L * (5 if F == 2 else 6) + 8)
+                a = loads / (ms / 1e3)
+                r["gather_rate"] = {"loads_per_launch": loads, "achieved_per_s": a,
+                                    "peak_per_s": l2pk["gather_loads_per_s"], "frac": a / l2pk["gather_loads_per_s"],
+                                    "peak_kind": "measured (scattered 16-byte loads, 32 MiB)"}
         elif kind == "mlp":
             peak_t = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
             ach_t = flops / (ms / 1e3) / 1e12
@@ -234,6 +269,13 @@ def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d, L, F)
                             "(the 64 MiB FP32 table gradient stays resident); the tensor pipe is not the limit")
             r["tensor"] = {"achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s", "frac": ach_t / peak_t,
                            "algorithmic_flops_per_launch": flops}
+            if l2pk:  # 6 vector reductions per point and level at F = 2 (x-paired), 8 at F = 4
+                reds = batch * L * (6 if F == 2 else 8)
+                a = reds / (ms / 1e3)
+                r["scatter_rate"] = {"reductions_per_launch": reds, "achieved_per_s": a,
+                                     "peak_per_s": l2pk["scatter_reductions_per_s"],
+                                     "frac": a / l2pk["scatter_reductions_per_s"],
+                                     "peak_kind": "measured (scattered 16-byte FP32 reductions, 64 MiB)"}
         return r
     ach = flops / (ms / 1e3) / 1e12
     if prec == "fp32":
@@ -288,7 +330,7 @@ def run_ours(args):
     clocks = Clocks(local)
     clocks.start()
     net.profile(True)
-    for k in ("mlp", "adam", "finish", "encode"):
+    for k in ("mlp", "adam", "finish", "encode", "scatter"):
         net.profile_read(k)
     barrier(ws)
     torch.cuda.synchronize()
@@ -340,14 +382,17 @@ def run_ours(args):
     if rank != 0:
         return 0
     pk, pk_kind = peaks()
-    kt = {k: net.profile_read(k) for k in ("encode",)}
+    l2pk = l2_peaks(nv, torch)
+    kt = {k: net.profile_read(k) for k in ("encode", "scatter")}
     kt["mlp"], kt["adam"], kt["finish"] = k_mlp, k_adam, k_fin
     avg = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in kt.items()}
     n_params, n_table = net.n_params, net.n_table
     d = c.dims
     D0 = d[0]
-    roof = roofline_of(max(("encode", "mlp", "adam"), key=lambda k: kt[k][0]), avg, prec, pk, pk_kind,
-                       batch, n_params, n_table, d, c.L, c.F)
+    dom = max(("encode", "mlp", "adam"), key=lambda k: kt[k][0])
+    roof = roofline_of(dom, avg, prec, pk, pk_kind, batch, n_params, n_table, d, c.L, c.F, l2pk)
+    roof_others = {k: roofline_of(k, avg, prec, pk, pk_kind, batch, n_params, n_table, d, c.L, c.F, l2pk)
+                   for k in ("encode", "mlp", "adam") if avg.get(k) and k != dom}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -358,9 +403,11 @@ def run_ours(args):
                    "l2": "working set > L2: each step's Adam streams params, grads, m, v (269 MB)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
+        "rooflines_other_kernels": roof_others,
+        "l2_access_peaks": l2pk,
         "kernels_ms_per_step": {k: v for k, v in avg.items() if v > 0},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": batch * 16, "d2h_bytes_per_step": 8},
-        "gpu_launches": args.steps * sum(1 for k in ("encode", "mlp", "adam", "finish") if kt[k][1]),
+        "gpu_launches": args.steps * sum(1 for k in ("encode", "mlp", "scatter", "adam", "finish") if kt[k][1]),
         "clocks": clk,
     }
     if ws == 1 and args.extras:

@@ -343,6 +343,20 @@ nv_status nv_render_raw_noalloc(const nv_volume *raw, const nv_camera *cam, cons
                                 const nv_macrocells *mc, const nv_render_opts *opts, float *rgba_dev,
                                 void *stream);
 
+/* ---- measurement (the paper has no counterpart) ---------------------------- */
+
+/* Reference rates for the rooflines of the scatter and the gather: `ops`
+ * (rounded up to a multiple of 8192) scattered 16-byte accesses to slots of a
+ * buffer of n16 16-byte slots (a power of two <= 2^32), each slot chosen by a
+ * 32-bit integer mixer of (thread, access, seed).  nv_peak_scatter adds
+ * (1, 1, 1, 1) to each chosen slot with an FP32 vector reduction (buf_dev:
+ * n16 x 4 floats, updated); nv_peak_gather loads each chosen slot (buf_dev:
+ * n16 x 16 bytes, read only; sink_dev: 1024 uint32 the kernel may write so the
+ * loads are kept).  Asynchronous on `stream`; time them with events. */
+nv_status nv_peak_scatter(float *buf_dev, int64_t n16, int64_t ops, uint64_t seed, void *stream);
+nv_status nv_peak_gather(const void *buf_dev, int64_t n16, int64_t ops, uint64_t seed, void *sink_dev,
+                         void *stream);
+
 /* ---- quality (Sec. 7) ------------------------------------------------------ */
 
 /* A-16: FP64 mean squared error over the RGB channels of two images,

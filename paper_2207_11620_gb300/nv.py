@@ -80,6 +80,8 @@ EXPORTS = {
     "nv_set_adam": ([C.c_void_p, C.POINTER(AdamCfg)], C.c_int),
     "nv_set_loss_scale": ([C.c_void_p, C.c_float], C.c_int),
     "nv_set_loss": ([C.c_void_p, C.c_int], C.c_int),
+    "nv_peak_scatter": ([C.c_void_p, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p], C.c_int),
+    "nv_peak_gather": ([C.c_void_p, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p], C.c_int),
     "nv_render_pt": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                       C.c_void_p], C.c_int),
     "nv_macrocells_reset": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p], C.c_int),
@@ -479,6 +481,23 @@ def render_inshader(net: NeuralVolume, cam: dict, lut, opts: dict, mc: tuple | N
     _check(lib().nv_render_inshader(net.handle, C.byref(c), _dev(lut, name="lut"), mp, C.byref(o),
                                     _dev(out, name="out"), sp))
     return out
+
+
+PEAK_OPS_QUANTUM = 8192  # accesses per CTA of the measurement kernels
+
+
+def peak_scatter(buf, ops, seed=0):
+    """Issue `ops` scattered 16-byte FP32 vector reductions into buf (float32 [n16, 4], n16 a power of two)."""
+    if buf.dim() != 2 or buf.shape[1] != 4:
+        raise ValueError("buf must be [n16, 4] float32")
+    _check(lib().nv_peak_scatter(_dev(buf, name="buf"), buf.shape[0], int(ops), int(seed), _stream()))
+
+
+def peak_gather(buf, ops, sink, seed=0):
+    """Issue `ops` scattered 16-byte loads from buf (any dtype, [n16 x 16 bytes]); sink: 1024 int32."""
+    n16 = buf.numel() * buf.element_size() // 16
+    _check(lib().nv_peak_gather(C.c_void_p(buf.data_ptr()), n16, int(ops), int(seed),
+                                _dev(sink, torch.int32, "sink"), _stream()))
 
 
 def image_mse(a, b, out=None):

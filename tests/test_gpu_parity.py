@@ -358,3 +358,18 @@ def test_image_and_volume_mse(nv):
     want = O.volume_mse(onet(cfg), params, vol)
     assert abs(got - want) <= FP32_TOL * want
     assert abs(O.psnr(got) - O.psnr(want)) < 1e-4
+
+
+# ------------------------------------------------------------ measurement ----
+
+def test_peak_kernels_touch_every_access_in_bounds(nv):
+    n16, ops = 1 << 12, 5 * nv.PEAK_OPS_QUANTUM
+    buf = torch.zeros((n16, 4), dtype=torch.float32, device="cuda")
+    nv.peak_scatter(buf, ops, seed=3)
+    torch.cuda.synchronize()
+    assert buf.double().sum().item() == 4.0 * ops  # every reduction landed (and only in buf)
+    assert (buf[:, 0] == buf[:, 3]).all().item()
+    assert (buf[:, 0] > 0).float().mean().item() > 0.99  # the mixer spreads the slots
+    sink = torch.zeros(1024, dtype=torch.int32, device="cuda")
+    nv.peak_gather(buf, ops, sink, seed=4)
+    torch.cuda.synchronize()
