@@ -188,7 +188,7 @@ def ncu_traffic(kernel):
         return None
     for line in open(p):
         f = line.split("#", 1)[0].split()
-        if len(f) == 2 and f[0] == kernel:
+        if len(f) >= 2 and f[0] == kernel:
             return int(f[1])
     return None
 
@@ -222,11 +222,13 @@ def l2_peaks(nv, torch):
                    "median of 5 launches (nv_peak_scatter / nv_peak_gather)"}
 
 
-def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d, L, F, l2pk=None):
+def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_visit, n_table, d, L, F, l2pk=None):
     """Roofline of one kernel of the config-2 step from its live average launch time.
 
     Algorithmic bytes / FLOPs per launch (per unit x units):
-      adam     34 B per parameter (read p, g, m, v; write p, m, v, g = 0, 16-bit shadow); 32 in FP32
+      adam     34 B per parameter it visits (read p, g, m, v; write p, m, v, g = 0, 16-bit shadow);
+               32 in FP32.  n_visit: the parameters in blocks that hold a weight or a hash slot a
+               point of [0,1]^3 can reach (nv_adam_span); the other blocks stay unchanged
       encode   per point: 8 corners x L levels x F 16-bit features read (8 L F 2 B) + the 16-bit
                feature row written (2 D0 B) + the trilinear target (8 voxels read, 4 B written)
       mlp      tensor-core path, per point: the feature row read (2 D0 B) + the target (4 B) + the
@@ -237,7 +239,7 @@ def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d, L, F,
     D0 = d[0]
     flops = 2 * batch * (D0 * 64 + 64 * 64) + 2 * batch * (2 * 64 * 64 + 2 * 64 * D0)
     if kind == "adam":
-        bytes_ = n_params * (32 + (2 if prec != "fp32" else 0))
+        bytes_ = n_visit * (32 + (2 if prec != "fp32" else 0))
         name = "k_adam"
     elif kind == "encode":
         bytes_ = batch * (8 * L * F * 2 + 2 * D0 + 8 * 4 + 4)
@@ -253,6 +255,8 @@ def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_params, n_table, d, L, F,
         r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
              "frac": ach / pk["hbm_gbs"], "traffic": ncu_traffic(name), "peak_kind": pk_kind + " (copy)",
              "algorithmic_bytes_per_launch": bytes_, "avg_ms": ms}
+        if kind == "adam":
+            r["params_visited_per_launch"] = n_visit
         if kind == "encode":
             r["limiter"] = ("L1-to-L2 request rate of the scattered 32-byte sector gathers; coarse levels hit "
                             "in L1 and the 16-bit tables in L2, so DRAM carries a fraction of these bytes")
@@ -387,20 +391,23 @@ def run_ours(args):
     kt["mlp"], kt["adam"], kt["finish"] = k_mlp, k_adam, k_fin
     avg = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in kt.items()}
     n_params, n_table = net.n_params, net.n_table
+    n_visit = net.adam_span()
     d = c.dims
     D0 = d[0]
     dom = max(("encode", "mlp", "adam"), key=lambda k: kt[k][0])
-    roof = roofline_of(dom, avg, prec, pk, pk_kind, batch, n_params, n_table, d, c.L, c.F, l2pk)
-    roof_others = {k: roofline_of(k, avg, prec, pk, pk_kind, batch, n_params, n_table, d, c.L, c.F, l2pk)
+    roof = roofline_of(dom, avg, prec, pk, pk_kind, batch, n_visit, n_table, d, c.L, c.F, l2pk)
+    roof_others = {k: roofline_of(k, avg, prec, pk, pk_kind, batch, n_visit, n_table, d, c.L, c.F, l2pk)
                    for k in ("encode", "mlp", "adam") if avg.get(k) and k != dom}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[prec], "data": "synthetic",
         "config": {"workload": "cfg2 training step: 128^3 blob volume, L16 F2 T2^19 Nmin16 b1.38, MLP 32-64-64-1, "
-                               "2^18 points sampled on the GPU, L2 loss, dense Adam",
+                               "2^18 points sampled on the GPU, L2 loss, Adam",
                    "global_batch": ws * batch, "mlp_precision": prec, "n_params": n_params,
-                   "l2": "working set > L2: each step's Adam streams params, grads, m, v (269 MB)",
+                   "adam_params_visited": n_visit,
+                   "l2": "working set > L2: each step's Adam streams params, grads, m, v of the visited "
+                         "blocks (%.0f MB)" % (n_visit * 16 / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
         "rooflines_other_kernels": roof_others,

@@ -137,7 +137,8 @@ nv_status nv_get_params(nv_ctx *ctx, float *params_any);
 /* Device pointer and length of an internal FP32 buffer (nv_buffer); owned by the context.
  * Writes through the params pointer do not reach the FP16/BF16 shadow (Adam
  * rewrites the shadow only of the parameters it changes): set parameters with
- * nv_set_params. */
+ * nv_set_params.  Handing out NV_BUF_GRADS, NV_BUF_ADAM_M or NV_BUF_ADAM_V
+ * makes every later optimizer step visit all parameters (nv_adam_span). */
 nv_status nv_buffer_ptr(nv_ctx *ctx, int which, float **ptr_dev, int64_t *n);
 /* Adam hyper-parameters (App. B lists beta 0.9 / 0.999, eps 1e-15). */
 nv_status nv_set_adam(nv_ctx *ctx, const nv_adam_cfg *cfg);
@@ -151,6 +152,15 @@ nv_status nv_set_loss_scale(nv_ctx *ctx, float scale);
 /* Optimizer steps taken (skipped ones not counted) and the current loss scale;
  * synchronises the context stream. */
 nv_status nv_get_step(nv_ctx *ctx, int *step, float *loss_scale);
+/* Parameters the next optimizer step visits (*n_visit).  Adam (Kingma & Ba,
+ * App. B settings) leaves a parameter with zero gradient and zero moments
+ * unchanged when there is no L2 term, so it skips the 128-parameter blocks
+ * that hold no weight and no hash slot a cell corner of a point in [0,1]^3 can
+ * map to (on coarse levels most of them); the result equals the dense update
+ * bit for bit.  It visits all n_params for good once an L2 term is used, a
+ * gradient or moment buffer was handed out by nv_buffer_ptr, or a gradient was
+ * scattered from a point outside [0,1]^3.  Synchronises the context stream. */
+nv_status nv_adam_span(nv_ctx *ctx, int64_t *n_visit);
 
 /* ---- network evaluation (Sec. 3.1) ---------------------------------------- */
 
@@ -168,8 +178,9 @@ nv_status nv_infer(nv_ctx *ctx, const float *xyz_dev, int64_t n, float *y_dev);
  * gradient into dparams_dev [n_params] (NULL: the context's NV_BUF_GRADS). */
 nv_status nv_backward(nv_ctx *ctx, const float *xyz_dev, int64_t n, const float *dL_dy_dev,
                       float *dparams_dev);
-/* A-8: one Adam step over every parameter (dense) from NV_BUF_GRADS, which it
- * zeroes; refreshes the FP16/BF16 shadow. */
+/* A-8: one Adam step over every parameter (dense, up to the blocks that
+ * nv_adam_span describes, which it would leave unchanged) from NV_BUF_GRADS,
+ * which it zeroes; refreshes the FP16/BF16 shadow. */
 nv_status nv_optimizer_step(nv_ctx *ctx);
 
 /* ---- training (Sec. 4) ---------------------------------------------------- */

@@ -19,7 +19,8 @@ namespace {
 template <int F, bool BF>
 __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t *__restrict__ shadow, PointSrc ps,
                                                       ChunkSpan cs, uint8_t *__restrict__ feat,
-                                                      float *__restrict__ tgt, float *__restrict__ xyz_out) {
+                                                      float *__restrict__ tgt, float *__restrict__ xyz_out,
+                                                      int *off_flag) {
   const int D0 = nd.dims[0];
   const int C = D0 / 8;
   const int64_t n = chunk_count(cs);
@@ -35,6 +36,8 @@ __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t
   }
   const float3 x = point_at(ps, cs.off + q);
   if (c == 0) {
+    if (off_flag && !(x.x >= 0.f && x.x <= 1.f && x.y >= 0.f && x.y <= 1.f && x.z >= 0.f && x.z <= 1.f))
+      *off_flag = 1;  // its corners may lie outside the vertex range of the optimizer's block list
     if (tgt) tgt[q] = nv_trilinear(ps.vol.data_dev, ps.vol.nx, ps.vol.ny, ps.vol.nz, x.x, x.y, x.z);
     if (xyz_out) {
       xyz_out[3 * q] = x.x;
@@ -63,8 +66,9 @@ inline unsigned grid_for(int64_t items) { return (unsigned)((items + 255) / 256)
 
 // tgt (nullable): [cap] targets of a Philox training sample (ps.kind == 2);
 // xyz_out (nullable): [cap][3] its points, for the MLP kernel's scatter.
+// off_flag (nullable): set to 1 when a point lies outside [0,1]^3.
 nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat,
-                              float *tgt, float *xyz_out) {
+                              float *tgt, float *xyz_out, int *off_flag) {
   const int C = c->nd.dims[0] / 8;
   const int64_t npad = (cs.cap + 127) & ~int64_t(127);
   if (npad == 0) return NV_OK;
@@ -73,12 +77,12 @@ nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSp
   const bool bf = c->prec == NV_BF16;
   switch (c->nd.F) {
     case 2:
-      if (bf) k_encode_tiles<2, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out);
-      else k_encode_tiles<2, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out);
+      if (bf) k_encode_tiles<2, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
+      else k_encode_tiles<2, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
       break;
     case 4:
-      if (bf) k_encode_tiles<4, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out);
-      else k_encode_tiles<4, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out);
+      if (bf) k_encode_tiles<4, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
+      else k_encode_tiles<4, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
       break;
     default:
       return nv_fail(NV_ERR_UNSUPPORTED, "tensor-core encode: F=%d", c->nd.F);

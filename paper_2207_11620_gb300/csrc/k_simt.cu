@@ -274,6 +274,8 @@ __global__ void __launch_bounds__(kP) k_mlp_f32(NetDesc nd, const float *__restr
         }
       } else if (valid) {
         // df = W_0^T delta_0, scattered level by level into the table gradients
+        if (!(x >= 0.f && x <= 1.f && y >= 0.f && y <= 1.f && z >= 0.f && z <= 1.f))
+          a.ds->off_domain = 1;  // corners outside the vertex range the optimizer's block list covers
         for (int l = 0; l < nd.L; ++l) {
           float df[F];
 #pragma unroll

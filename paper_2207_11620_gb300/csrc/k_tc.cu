@@ -34,7 +34,7 @@
 #include "tc_ptx.cuh"
 
 nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat,
-                              float *tgt, float *xyz_out);
+                              float *tgt, float *xyz_out, int *off_flag);
 
 namespace {
 
@@ -616,10 +616,13 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
   const bool sampled = mode == MODE_TRAIN && ps.kind == 2;
   float *tgt = sampled ? c->tc_tgt : nullptr;
   float *xyz_out = sampled ? c->tc_xyz : nullptr;
+  // given points of a pass that scatters table gradients: the gather kernel
+  // flags any outside [0,1]^3 (sampled ones never are)
+  int *off_flag = (mode == MODE_TRAIN || mode == MODE_BACKWARD) && ps.kind == 0 ? &c->ds->off_domain : nullptr;
   for (int64_t off = 0; off < n_upper; off += c->tc_cap) {
     ChunkSpan cs{n_dev, n_mult, a.n, off, n_upper - off < c->tc_cap ? n_upper - off : c->tc_cap};
     int tk = prof_begin(c);
-    s = launch_encode_tiles(c, ps, cs, c->tc_feat, tgt, xyz_out);
+    s = launch_encode_tiles(c, ps, cs, c->tc_feat, tgt, xyz_out, off_flag);
     prof_end(c, NV_K_ENCODE, tk);
     if (s != NV_OK) return s;
     tk = prof_begin(c);

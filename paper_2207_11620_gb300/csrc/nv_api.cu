@@ -88,6 +88,7 @@ static void ctx_free(nv_ctx *c) {
   cudaFree(c->tc_feat);
   cudaFree(c->tc_tgt);
   cudaFree(c->tc_xyz);
+  cudaFree(c->adam_blocks);
   delete c;
 }
 
@@ -171,6 +172,11 @@ extern "C" nv_status nv_create(int L, int F, int log2T, int Nmin, double b, cons
     ctx_free(c);
     return s;
   }
+  nv_status sb = build_adam_blocks(c);
+  if (sb != NV_OK) {
+    ctx_free(c);
+    return sb;
+  }
   *out = c;
   return NV_OK;
 }
@@ -222,6 +228,8 @@ extern "C" nv_status nv_buffer_ptr(nv_ctx *c, int which, float **ptr, int64_t *n
     case NV_BUF_ADAM_V: *ptr = c->adam_v; break;
     default: return nv_fail(NV_ERR_ARG, "nv_buffer_ptr: unknown buffer %d", which);
   }
+  // whoever holds the gradient or a moment may write any slot: Adam visits all from now on
+  if (which != NV_BUF_PARAMS) c->adam_dense = 1;
   if (n) *n = c->n_params;
   return NV_OK;
 }
@@ -247,6 +255,25 @@ extern "C" nv_status nv_set_loss_scale(nv_ctx *c, float scale) {
   if (!c || !(scale > 0.f) || !std::isfinite(scale)) return nv_fail(NV_ERR_ARG, "nv_set_loss_scale: bad scale");
   NV_CUDA(cudaStreamSynchronize(c->stream), "nv_set_loss_scale: sync");
   NV_CUDA(cudaMemcpy(&c->ds->loss_scale, &scale, sizeof(float), cudaMemcpyHostToDevice), "nv_set_loss_scale");
+  return NV_OK;
+}
+
+extern "C" nv_status nv_adam_span(nv_ctx *c, int64_t *n_visit) {
+  if (!c || !n_visit) return nv_fail(NV_ERR_ARG, "nv_adam_span: NULL argument");
+  int off = 0;
+  NV_CUDA(cudaStreamSynchronize(c->stream), "nv_adam_span: sync");
+  NV_CUDA(cudaMemcpy(&off, &c->ds->off_domain, sizeof(int), cudaMemcpyDeviceToHost), "nv_adam_span: copy");
+  if (!c->adam_blocks || c->adam_dense || off || c->adam.l2_reg != 0.f) {
+    *n_visit = c->n_params;
+  } else {  // the blocks visited, the last one clipped to the vectorised part, plus the scalar tail
+    const int64_t n4 = c->n_params >> 2;
+    int32_t last = 0;
+    NV_CUDA(cudaMemcpy(&last, c->adam_blocks + c->adam_nblocks - 1, sizeof(int32_t), cudaMemcpyDeviceToHost),
+            "nv_adam_span: copy");
+    int64_t v = c->adam_nblocks * 128;
+    if ((int64_t)last * 32 + 32 > n4) v -= ((int64_t)last * 32 + 32 - n4) * 4;
+    *n_visit = v + (c->n_params - 4 * n4);
+  }
   return NV_OK;
 }
 

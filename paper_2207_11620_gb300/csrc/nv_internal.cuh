@@ -35,6 +35,7 @@ struct DevState {
   float loss_scale;   // static loss scale of the tensor-core backward
   int err;            // set by a kernel whose bounded wait ran out
   unsigned adam_done; // CTAs of the running Adam launch that have finished (the last one resets it)
+  int off_domain;     // set (for good) when a table gradient was scattered from a point outside [0,1]^3
 };
 
 struct nv_ctx {
@@ -61,6 +62,9 @@ struct nv_ctx {
   float *tc_tgt;                            // tensor-core path: one chunk of sampled training targets
   float *tc_xyz;                            // tensor-core path: the points of that chunk [cap][3]
   int64_t tc_cap;                           // points per chunk of the two above
+  int32_t *adam_blocks;                     // sorted 128-parameter blocks Adam visits (NULL: all of them)
+  int64_t adam_nblocks;                     // entries of adam_blocks
+  int adam_dense;                           // 1: Adam visits every block from now on (sticky)
 };
 
 // Kernel timing hooks (nv_api.cu): bracket a launch on the context stream.
@@ -270,6 +274,7 @@ bool tc_supported(const NetDesc &nd);
 // Adam over all parameters; its last CTA counts the step (or halves the loss
 // scale after an overflow) and publishes loss_acc * inv_n into loss_out.
 nv_status launch_adam(nv_ctx *c, double inv_n, double *loss_out);
+nv_status build_adam_blocks(nv_ctx *c);
 nv_status launch_scale_double(double *x, double s, cudaStream_t st);
 nv_status launch_shadow(nv_ctx *c);
 // sampling, macrocells, rendering, reductions

@@ -93,6 +93,7 @@ EXPORTS = {
     "nv_render_inshader": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
                            C.c_int),
     "nv_get_step": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float)], C.c_int),
+    "nv_adam_span": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "nv_hash_indices": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "nv_encode": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "nv_infer": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
@@ -293,6 +294,12 @@ class NeuralVolume:
         st, ls = C.c_int(), C.c_float()
         _check(lib().nv_get_step(self._h, C.byref(st), C.byref(ls)))
         return st.value, ls.value
+
+    def adam_span(self):
+        """Parameters the next optimizer step visits (all of them once dense)."""
+        v = C.c_int64()
+        _check(lib().nv_adam_span(self._h, C.byref(v)))
+        return v.value
 
     def hash_indices(self, xyz):
         p, n = _points(xyz)
