@@ -74,6 +74,18 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
   return pol;
 }
 
+// b^e for an integer e >= 0 by binary exponentiation: about 2 log2(e) FP64
+// multiplies (the library pow's FP64 log and exp took ~6 us of dependent FP64
+// work on this GPU at the head of every launch); within a few ulps of pow.
+__device__ __forceinline__ double ipow(double b, int e) {
+  double r = 1.0;
+  for (; e > 0; e >>= 1) {
+    if (e & 1) r *= b;
+    b *= b;
+  }
+  return r;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
 }
@@ -119,18 +131,11 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(float *__restrict__ p, fl
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)kStages * kStageF4 * 16);
   uint64_t *empty = full + kStages;
   int64_t *ids = reinterpret_cast<int64_t *>(empty + kStages);  // [kStages][kCW] block of each slot, -1: none
-  // bias corrections of step t (Kingma & Ba) and the decayed learning rate of
-  // step index t - 1 (App. B): one FP64 evaluation per CTA
   __shared__ float s_bc[3];
-  __shared__ int s_skip, s_all;
+  __shared__ int s_skip, s_all, s_step;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    const int t = ds->step + 1;
-    s_bc[0] = (float)(1.0 / (1.0 - pow((double)hp.b1, (double)t)));
-    s_bc[1] = (float)(1.0 / (1.0 - pow((double)hp.b2, (double)t)));
-    const int k = t - 1;
-    const int d = (k < hp.decay_start || hp.decay_interval <= 0) ? 0 : (k - hp.decay_start) / hp.decay_interval + 1;
-    s_bc[2] = (float)((double)hp.lr * pow((double)hp.decay_base, (double)d));
+    s_step = ds->step;
     s_skip = ds->overflow != 0;
     s_all = blocks == nullptr || ds->off_domain != 0;
     for (int st = 0; st < kStages; ++st) {
@@ -206,6 +211,18 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam(float *__restrict__ p, fl
     }
   } else {
     // ---- consumers: warp w updates block w of each tile ----
+    // bias corrections of step t (Kingma & Ba) and the decayed learning rate
+    // of step index t - 1 (App. B): one FP64 evaluation per CTA, while the
+    // producer's first copies are in flight (t >= 1, d >= 0)
+    if (threadIdx.x == 0) {
+      const int t = s_step + 1;
+      s_bc[0] = (float)(1.0 / (1.0 - ipow((double)hp.b1, t)));
+      s_bc[1] = (float)(1.0 / (1.0 - ipow((double)hp.b2, t)));
+      const int k = t - 1;
+      const int d = (k < hp.decay_start || hp.decay_interval <= 0) ? 0 : (k - hp.decay_start) / hp.decay_interval + 1;
+      s_bc[2] = (float)((double)hp.lr * ipow((double)hp.decay_base, d));
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(kCW * 32) : "memory");  // the consumer warps only
     const float inv_bc1 = s_bc[0], inv_bc2 = s_bc[1], lr = s_bc[2];
     float4 *po = reinterpret_cast<float4 *>(p), *mo = reinterpret_cast<float4 *>(m);
     float4 *vo = reinterpret_cast<float4 *>(v);
