@@ -244,48 +244,60 @@ double or_lr_at(double lr0, int k, int start, int interval, double base) {
   return lr0 * pow(base, (double)((k - start) / interval + 1));
 }
 
+/* A-6 for one point: the network's forward at x (act: every layer's
+ * activations), then the chain rule from dL/dy back to the input features.
+ * dz_out = dL/dy * y (1 - y); dW_k += delta_k a_k^T (when gw is given);
+ * delta_{k-1} = (W_k^T delta_k) * 1[z > 0]; df = W_0^T delta_0, left in
+ * delta[0 .. L*F). */
+static void or_point_df(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
+                        const double *params, const float *x, double dL_dy, double *gw,
+                        double *act, double *delta, double *din) {
+  uint32_t T = 1u << log2T;
+  const double *weights = params + (int64_t)L * T * F;
+  int nl = n_dims - 1;
+  or_encode_point(L, F, log2T, res, params, x, act);
+  double y = or_mlp_point(dims, n_dims, weights, act);
+  delta[0] = dL_dy * y * (1.0 - y);
+  /* walk the layers from the output back to the input */
+  for (int k = nl - 1; k >= 0; --k) {
+    int ind = dims[k], outd = dims[k + 1];
+    int64_t woff = 0, aoff = 0;
+    for (int q = 0; q < k; ++q) { woff += (int64_t)dims[q] * dims[q + 1]; aoff += dims[q]; }
+    const double *Wk = weights + woff;
+    const double *ak = act + aoff;
+    if (gw) {
+      double *gWk = gw + woff;
+      for (int j = 0; j < outd; ++j)
+        for (int c = 0; c < ind; ++c) gWk[(int64_t)j * ind + c] += delta[j] * ak[c];
+    }
+    for (int c = 0; c < ind; ++c) {
+      double s = 0.0;
+      for (int j = 0; j < outd; ++j) s += Wk[(int64_t)j * ind + c] * delta[j];
+      /* a_k = ReLU(z_k) for k > 0, so 1[z_k > 0] == 1[a_k > 0] */
+      din[c] = (k > 0) ? (ak[c] > 0.0 ? s : 0.0) : s;
+    }
+    memcpy(delta, din, sizeof(double) * ind);
+  }
+}
+
 /* A-6 / A-7: analytic backward of encode + MLP for upstream gradients dL/dy.
- * Accumulates (+=) into grads, laid out like params (tables then weights).
- * Chain rule: dz_out = dL/dy * y (1 - y); dW_k += delta_k a_k^T;
- * delta_{k-1} = (W_k^T delta_k) * 1[z > 0]; df = W_0^T delta_0; the table
- * gradient of every corner gets its trilinear weight times df (the adjoint of
- * A-3).  Serial: the scatter into shared table entries is order dependent. */
+ * Accumulates (+=) into grads, laid out like params (tables then weights):
+ * the weight gradients of or_point_df, and for every corner of every level
+ * its trilinear weight times df (the adjoint of A-3).  Serial: the scatter
+ * into shared table entries is order dependent. */
 void or_backward(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
                  const double *params, const float *xyz, int64_t n, const double *dL_dy,
                  double *grads) {
   uint32_t T = 1u << log2T;
   int64_t tab = (int64_t)L * T * F;
-  const double *weights = params + tab;
-  double *gw = grads + tab;
   int alen = or_act_len(dims, n_dims);
   int mx = or_max_dim(dims, n_dims);
   double *act = (double *)malloc(sizeof(double) * alen);
   double *delta = (double *)malloc(sizeof(double) * mx);
   double *din = (double *)malloc(sizeof(double) * mx);
-  int nl = n_dims - 1;
   for (int64_t i = 0; i < n; ++i) {
     const float *x = xyz + 3 * i;
-    or_encode_point(L, F, log2T, res, params, x, act);
-    double y = or_mlp_point(dims, n_dims, weights, act);
-    delta[0] = dL_dy[i] * y * (1.0 - y);
-    /* walk the layers from the output back to the input */
-    for (int k = nl - 1; k >= 0; --k) {
-      int ind = dims[k], outd = dims[k + 1];
-      int64_t woff = 0, aoff = 0;
-      for (int q = 0; q < k; ++q) { woff += (int64_t)dims[q] * dims[q + 1]; aoff += dims[q]; }
-      const double *Wk = weights + woff;
-      const double *ak = act + aoff;
-      double *gWk = gw + woff;
-      for (int j = 0; j < outd; ++j)
-        for (int c = 0; c < ind; ++c) gWk[(int64_t)j * ind + c] += delta[j] * ak[c];
-      for (int c = 0; c < ind; ++c) {
-        double s = 0.0;
-        for (int j = 0; j < outd; ++j) s += Wk[(int64_t)j * ind + c] * delta[j];
-        /* a_k = ReLU(z_k) for k > 0, so 1[z_k > 0] == 1[a_k > 0] */
-        din[c] = (k > 0) ? (ak[c] > 0.0 ? s : 0.0) : s;
-      }
-      memcpy(delta, din, sizeof(double) * ind);
-    }
+    or_point_df(L, F, log2T, res, dims, n_dims, params, x, dL_dy[i], grads + tab, act, delta, din);
     /* delta now holds df (length L*F): scatter into the table gradients */
     for (int l = 0; l < L; ++l) {
       int64_t c[3]; double w[3];
@@ -300,6 +312,52 @@ void or_backward(int L, int F, int log2T, const int *res, const int *dims, int n
     }
   }
   free(act); free(delta); free(din);
+}
+
+/* Gradient of the loss with respect to the point coordinates: dxyz[i][a] =
+ * dL/dx_a.  Within a cell of level l the trilinear weights are products of
+ * w_a or 1 - w_a with w_a = x_a N_l - c_a, so d(weight)/dx_a = N_l times the
+ * product of the other two axes' factors, signed + for the upper corner and -
+ * for the lower one (the FP32 rounding of x N_l is taken as having slope N_l).
+ * dL/dx_a = sum over levels and corners of that derivative times the dot
+ * product of the corner's table entry with df_l. */
+void or_backward_x(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
+                   const double *params, const float *xyz, int64_t n, const double *dL_dy,
+                   double *dxyz) {
+  uint32_t T = 1u << log2T;
+  int alen = or_act_len(dims, n_dims);
+  int mx = or_max_dim(dims, n_dims);
+#pragma omp parallel
+  {
+    double *act = (double *)malloc(sizeof(double) * alen);
+    double *delta = (double *)malloc(sizeof(double) * mx);
+    double *din = (double *)malloc(sizeof(double) * mx);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      const float *x = xyz + 3 * i;
+      or_point_df(L, F, log2T, res, dims, n_dims, params, x, dL_dy[i], NULL, act, delta, din);
+      double gx[3] = {0.0, 0.0, 0.0};
+      for (int l = 0; l < L; ++l) {
+        int64_t c[3]; double w[3];
+        for (int a = 0; a < 3; ++a) or_cell(x[a], res[l], &c[a], &w[a]);
+        for (int d = 0; d < 8; ++d) {
+          int dd[3] = {d & 1, (d >> 1) & 1, (d >> 2) & 1};
+          uint32_t h = or_hash(c[0] + dd[0], c[1] + dd[1], c[2] + dd[2], T);
+          const double *e = params + ((int64_t)l * T + h) * F;
+          double dot = 0.0;
+          for (int j = 0; j < F; ++j) dot += e[j] * delta[l * F + j];
+          for (int a = 0; a < 3; ++a) {
+            double dw = dd[a] ? 1.0 : -1.0;
+            for (int o = 0; o < 3; ++o)
+              if (o != a) dw *= dd[o] ? w[o] : 1.0 - w[o];
+            gx[a] += (double)res[l] * dw * dot;
+          }
+        }
+      }
+      for (int a = 0; a < 3; ++a) dxyz[3 * i + a] = gx[a];
+    }
+    free(act); free(delta); free(din);
+  }
 }
 
 /* A-8: textbook Adam (Kingma & Ba), as the paper's optimizer (Sec. 3.1, App. B),

@@ -78,6 +78,8 @@ def lib():
         L.or_lr_at.restype = C.c_double
         L.or_backward.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
                                   C.c_int64, _f64p, _f64p]
+        L.or_backward_x.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
+                                    C.c_int64, _f64p, _f64p]
         L.or_adam.argtypes = [_f64p, _f64p, _f64p, _f64p, C.c_int64, C.c_int, C.c_double,
                               C.c_double, C.c_double, C.c_double, C.c_double]
         L.or_train_step.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f64p,
@@ -240,6 +242,15 @@ def backward(net: Net, params, xyz, dL_dy):
     lib().or_backward(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims), _f64(params),
                       xyz, xyz.shape[0], _f64(dL_dy), g)
     return g
+
+
+def backward_x(net: Net, params, xyz, dL_dy):
+    """dL/dx of every point, [n][3] float64 (the coordinate gradient)."""
+    xyz = _f32(xyz)
+    out = np.zeros((xyz.shape[0], 3), dtype=np.float64)
+    lib().or_backward_x(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims), _f64(params),
+                        xyz, xyz.shape[0], _f64(dL_dy), out)
+    return out
 
 
 def adam(p, g, m, v, t, lr=1e-2, b1=0.9, b2=0.999, eps=1e-15, l2=0.0):

@@ -207,6 +207,91 @@ def test_backward_untouched_entries_zero():
     assert np.all(gt[~touched] == 0)
 
 
+def _grid_points(n, q, seed, net, h):
+    """Points on the 2^-q lattice (x N_l and x +- h then stay exact in FP32 for
+    N_l < 2^(24-q)) whose cells at every level are the same at x - h and x + h
+    on every axis, so the trilinear weights are linear in x over [x - h, x + h]."""
+    rng = np.random.default_rng(seed)
+    res = net.res
+    out = []
+    while len(out) < n:
+        x = rng.integers(1, (1 << q) - 1, size=3) / float(1 << q)
+        ok = all(np.floor((x - h) * N).tolist() == np.floor((x + h) * N).tolist() for N in res)
+        if ok:
+            out.append(x)
+    return np.array(out, dtype=np.float32)
+
+
+def _coord_fd(net, params, x, dy, h):
+    fd = np.zeros((x.shape[0], 3))
+    for a in range(3):
+        xp, xm = x.copy(), x.copy()
+        xp[:, a] += np.float32(h)
+        xm[:, a] -= np.float32(h)
+        fd[:, a] = dy * (O.forward(net, params, xp) - O.forward(net, params, xm)) / (2 * h)
+    return fd
+
+
+def test_coordinate_gradient_matches_finite_differences():
+    """Non-negative tables and weights keep every ReLU in its linear part, so
+    y is smooth in x; within one cell per level the trilinear weights are
+    linear, and central differences on an exact FP32 lattice leave only the
+    O(h^2) curvature of the sigmoid."""
+    net = O.Net(L=4, F=2, log2T=10, Nmin=4, b=1.5, dims=(8, 16, 16, 1))
+    params = np.abs(I.uniform_params(net.n_params, seed=31, scale=0.5)).astype(np.float64)
+    h = 2.0 ** -15
+    x = _grid_points(40, 15, 32, net, h)
+    dy = np.random.default_rng(33).normal(size=x.shape[0])
+    g = O.backward_x(net, params, x, dy)
+    fd = _coord_fd(net, params, x, dy, h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9 * np.abs(fd).max())
+    assert np.abs(g).min() > 0  # every axis carries a gradient
+
+
+def test_coordinate_gradient_at_config1_scale():
+    """Config 1's shape (8 levels up to N = 273, T = 2^14 with hash collisions)
+    with non-negative parameters (every ReLU linear, so y is smooth): central
+    differences agree up to their O((N h)^2) curvature term."""
+    net = O.Net(L=8, F=2, log2T=14, Nmin=16, b=1.5, dims=(16, 64, 64, 1))
+    params = np.abs(I.uniform_params(net.n_params, seed=34)).astype(np.float64)
+    h = 2.0 ** -15
+    x = _grid_points(60, 15, 35, net, h)
+    dy = np.random.default_rng(37).normal(size=x.shape[0])
+    g = O.backward_x(net, params, x, dy)
+    fd = _coord_fd(net, params, x, dy, h)
+    np.testing.assert_allclose(g, fd, rtol=1e-4, atol=1e-7 * np.abs(fd).max())
+
+
+def test_coordinate_gradient_of_a_ramp_is_closed_form():
+    """A one-level, one-feature network whose table holds the ramp 0.1 i at
+    vertex (i, j, k): trilinear interpolation reproduces the ramp exactly,
+    f = 0.8 x, and with one hidden unit (weights w_in, w_out > 0, so the ReLU
+    is the identity on f >= 0) y = sigmoid(w_out w_in 0.8 x): dy/dx has a
+    closed form and dy/dy, dy/dz are zero."""
+    net = O.Net(L=1, F=1, log2T=16, Nmin=8, b=1.0, dims=(1, 1, 1))
+    T = net.T
+    params = np.zeros(net.n_params)
+    # table entry of vertex (i, j, k) = 0.1 * i (a ramp in x), via the hash of each vertex
+    for i in range(9):
+        for j in range(9):
+            for k in range(9):
+                hsh = (i ^ ((j * 2654435761) & 0xFFFFFFFF) ^ ((k * 805459861) & 0xFFFFFFFF)) & (T - 1)
+                params[hsh] = 0.1 * i
+    w_in, w_out = 0.7, 1.3
+    params[net.n_table:] = [w_in, w_out]
+    x = _grid_points(10, 12, 36, net, 2.0 ** -12)
+    # the ramp needs no collisions among the 729 vertices in 2^16 slots; check it
+    hs = {(i ^ ((j * 2654435761) & 0xFFFFFFFF) ^ ((k * 805459861) & 0xFFFFFFFF)) & (T - 1)
+          for i in range(9) for j in range(9) for k in range(9)}
+    assert len(hs) == 729
+    g = O.backward_x(net, params, x, np.ones(x.shape[0]))
+    f = 0.1 * 8 * x[:, 0].astype(np.float64)                # the interpolated ramp
+    y = 1.0 / (1.0 + np.exp(-w_out * w_in * f))
+    want_x = y * (1 - y) * w_out * w_in * 0.1 * 8            # d/dx of sigmoid(w_out w_in 0.8 x)
+    np.testing.assert_allclose(g[:, 0], want_x, rtol=1e-12)
+    np.testing.assert_allclose(g[:, 1:], 0.0, atol=1e-15)
+
+
 # ------------------------------------------------------------------ Adam ----
 
 def test_adam_first_step_is_signed_lr():
