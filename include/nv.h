@@ -175,9 +175,13 @@ nv_status nv_encode(nv_ctx *ctx, const float *xyz_dev, int64_t n, float *feat_de
 nv_status nv_infer(nv_ctx *ctx, const float *xyz_dev, int64_t n, float *y_dev);
 /* A-6/A-7: backward of nv_infer for upstream gradients dL_dy_dev [n]: recomputes
  * the forward (nothing is stored between the calls) and ADDS the parameter
- * gradient into dparams_dev [n_params] (NULL: the context's NV_BUF_GRADS). */
+ * gradient into dparams_dev [n_params] (NULL: the context's NV_BUF_GRADS).
+ * dxyz_dev (nullable): [n][3], WRITTEN with dL/dx of every point, the adjoint
+ * of the trilinear weights of A-3 (within a cell of level l, d w_a / d x_a =
+ * N_l) applied to dL/df, with the FP32 master tables; the context keeps an
+ * [n][L*F] FP32 scratch for dL/df, grown on demand. */
 nv_status nv_backward(nv_ctx *ctx, const float *xyz_dev, int64_t n, const float *dL_dy_dev,
-                      float *dparams_dev);
+                      float *dparams_dev, float *dxyz_dev);
 /* A-8: one Adam step over every parameter (dense, up to the blocks that
  * nv_adam_span describes, which it would leave unchanged) from NV_BUF_GRADS,
  * which it zeroes; refreshes the FP16/BF16 shadow. */

@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(kP) k_mlp_f32(NetDesc nd, const float *__restr
             float s = 0.f;
             for (int j = 0; j < dout; ++j) s += W[j * din + i] * myd[j];
             df[jf] = s;
+            if (a.df_out) a.df_out[p * din + i] = s;
           }
           scatter_level<F>(a.grads + (size_t)l * nd.T * F, nd.T - 1, (float)nd.res[l], x, y, z, df);
         }
@@ -338,6 +339,56 @@ nv_status dispatch_f(const nv_ctx *c, const MlpArgs &a, const int *n_dev, int n_
   return nv_fail(NV_ERR_UNSUPPORTED, "F=%d (supported: 1, 2, 4, 8)", c->nd.F);
 }
 
+// Gradient of the loss in the point coordinates from dL/df (the Jacobian of
+// A-3): within a cell of level l, the weight of corner d is a product of w_a
+// or 1 - w_a with w_a = x_a N_l - c_a, so its derivative in x_a is N_l times
+// +1 (upper corner) or -1 (lower) times the other two axes' factors; dL/dx_a
+// sums that times <theta_l[h_d], dL/df_l> over levels and corners.  FP32
+// master tables, one thread per point.
+template <int F>
+__global__ void __launch_bounds__(256) k_coord_grad(NetDesc nd, const float *__restrict__ params,
+                                                    const float *__restrict__ xyz, int64_t n,
+                                                    const float *__restrict__ df, float *__restrict__ dxyz) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+  const int D0 = nd.L * F;
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  for (int l = 0; l < nd.L; ++l) {
+    const float N = (float)nd.res[l];
+    int cx, cy, cz;
+    float wx, wy, wz;
+    nv_cell(x, N, cx, wx);
+    nv_cell(y, N, cy, wy);
+    nv_cell(z, N, cz, wz);
+    float d[F];
+#pragma unroll
+    for (int j = 0; j < F; ++j) d[j] = df[i * D0 + l * F + j];
+    const float *tab = params + (size_t)l * nd.T * F;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+      const uint32_t h = nv_hash3((uint32_t)(cx + dx), (uint32_t)(cy + dy), (uint32_t)(cz + dz)) & (nd.T - 1);
+      float e[F];
+      load_entry<F>(tab + (size_t)h * F, e);
+      float dot = 0.f;
+#pragma unroll
+      for (int j = 0; j < F; ++j) dot += e[j] * d[j];
+      const float fx = dx ? wx : 1.f - wx, fy = dy ? wy : 1.f - wy, fz = dz ? wz : 1.f - wz;
+      sx += (dx ? fy : -fy) * fz * dot;
+      sy += (dy ? fx : -fx) * fz * dot;
+      sz += (dz ? fx : -fx) * fy * dot;
+    }
+    gx += N * sx;
+    gy += N * sy;
+    gz += N * sz;
+  }
+  dxyz[3 * i] = gx;
+  dxyz[3 * i + 1] = gy;
+  dxyz[3 * i + 2] = gz;
+}
+
 }  // namespace
 
 nv_status launch_hash_indices(const nv_ctx *c, const float *xyz, int64_t n, uint32_t *idx) {
@@ -374,4 +425,18 @@ nv_status launch_mlp_f32_ext(const nv_ctx *c, int mode, const MlpArgs &a, const 
 
 nv_status launch_mlp_f32(const nv_ctx *c, int mode, const MlpArgs &a) {
   return launch_mlp_f32_ext(c, mode, a, nullptr, 1, a.n, mode == MODE_TRAIN ? &a.ds->loss_acc : nullptr);
+}
+
+// df: [n][L*F] dL/df of nv_backward; dxyz: [n][3] written.
+nv_status launch_coord_grad(const nv_ctx *c, const float *xyz, int64_t n, const float *df, float *dxyz) {
+  if (n == 0) return NV_OK;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  switch (c->nd.F) {
+    case 1: k_coord_grad<1><<<blocks, 256, 0, c->stream>>>(c->nd, c->params, xyz, n, df, dxyz); break;
+    case 2: k_coord_grad<2><<<blocks, 256, 0, c->stream>>>(c->nd, c->params, xyz, n, df, dxyz); break;
+    case 4: k_coord_grad<4><<<blocks, 256, 0, c->stream>>>(c->nd, c->params, xyz, n, df, dxyz); break;
+    case 8: k_coord_grad<8><<<blocks, 256, 0, c->stream>>>(c->nd, c->params, xyz, n, df, dxyz); break;
+    default: return nv_fail(NV_ERR_UNSUPPORTED, "F=%d", c->nd.F);
+  }
+  return nv_cuda_check(cudaGetLastError(), "k_coord_grad launch");
 }

@@ -418,6 +418,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_mlp_tc(NetDesc nd, const float 
           df[i] *= inv_scale;
           if (!isfinite(df[i])) bad = true;
         }
+        if (MODE == MODE_BACKWARD && a.df_out) {  // this thread's half of dL/df, level-major
+          float4 *dst = reinterpret_cast<float4 *>(a.df_out + p * D0 + hh * DH);
+#pragma unroll
+          for (int i = 0; i < DH; i += 4) dst[i / 4] = make_float4(df[i], df[i + 1], df[i + 2], df[i + 3]);
+        }
         const float3 x = point_at(ps, p);
         if (nd.F == 2) {
 #pragma unroll

@@ -89,6 +89,7 @@ static void ctx_free(nv_ctx *c) {
   cudaFree(c->tc_tgt);
   cudaFree(c->tc_xyz);
   cudaFree(c->adam_blocks);
+  cudaFree(c->df_buf);
   delete c;
 }
 
@@ -322,7 +323,8 @@ extern "C" nv_status nv_infer(nv_ctx *c, const float *xyz, int64_t n, float *y) 
   return s;
 }
 
-extern "C" nv_status nv_backward(nv_ctx *c, const float *xyz, int64_t n, const float *dy, float *dparams) {
+extern "C" nv_status nv_backward(nv_ctx *c, const float *xyz, int64_t n, const float *dy, float *dparams,
+                                 float *dxyz) {
   NV_TRY(check_points(c, xyz, n, "nv_backward"));
   if (n > 0 && !dy) return nv_fail(NV_ERR_ARG, "nv_backward: dL_dy is NULL");
   if (n == 0) return NV_OK;
@@ -332,10 +334,29 @@ extern "C" nv_status nv_backward(nv_ctx *c, const float *xyz, int64_t n, const f
   a.n = n;
   a.grads = dparams ? dparams : c->grads;
   a.ds = c->ds;
-  if (c->prec != NV_FP32) return launch_mlp_tc(c, MODE_BACKWARD, a);  // times its kernels itself
+  if (dxyz) {  // dL/df of every point is kept for the coordinate gradient
+    const int64_t need = n * c->nd.dims[0];
+    if (c->df_cap < need) {
+      cudaFree(c->df_buf);
+      c->df_buf = nullptr;
+      c->df_cap = 0;
+      NV_CUDA(cudaMalloc(&c->df_buf, (size_t)need * sizeof(float)), "nv_backward: dL/df scratch");
+      c->df_cap = need;
+    }
+    a.df_out = c->df_buf;
+  }
+  if (c->prec != NV_FP32) {
+    NV_TRY(launch_mlp_tc(c, MODE_BACKWARD, a));  // times its kernels itself
+  } else {
+    int tk = prof_begin(c);
+    nv_status s = launch_mlp_f32(c, MODE_BACKWARD, a);
+    prof_end(c, NV_K_MLP, tk);
+    NV_TRY(s);
+  }
+  if (!dxyz) return NV_OK;
   int tk = prof_begin(c);
-  nv_status s = launch_mlp_f32(c, MODE_BACKWARD, a);
-  prof_end(c, NV_K_MLP, tk);
+  nv_status s = launch_coord_grad(c, xyz, n, c->df_buf, dxyz);
+  prof_end(c, NV_K_OTHER, tk);
   return s;
 }
 

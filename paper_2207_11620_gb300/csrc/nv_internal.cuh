@@ -65,6 +65,8 @@ struct nv_ctx {
   int32_t *adam_blocks;                     // sorted 128-parameter blocks Adam visits (NULL: all of them)
   int64_t adam_nblocks;                     // entries of adam_blocks
   int adam_dense;                           // 1: Adam visits every block from now on (sticky)
+  float *df_buf;                            // nv_backward with a coordinate gradient: dL/df [cap][L*F]
+  int64_t df_cap;
 };
 
 // Kernel timing hooks (nv_api.cu): bracket a launch on the context stream.
@@ -255,6 +257,7 @@ struct MlpArgs {
   uint32_t sample_step;
   float inv_n;           // TRAIN: 1/n of the batch mean
   int l1;                // TRAIN: L1 loss (else L2)
+  float *df_out;         // BACKWARD (nullable): dL/df of every point, [n][L*F] FP32
 };
 
 // FP32 CUDA-core path
@@ -274,6 +277,7 @@ bool tc_supported(const NetDesc &nd);
 // Adam over all parameters; its last CTA counts the step (or halves the loss
 // scale after an overflow) and publishes loss_acc * inv_n into loss_out.
 nv_status launch_adam(nv_ctx *c, double inv_n, double *loss_out);
+nv_status launch_coord_grad(const nv_ctx *c, const float *xyz, int64_t n, const float *df, float *dxyz);
 nv_status build_adam_blocks(nv_ctx *c);
 nv_status launch_scale_double(double *x, double s, cudaStream_t st);
 nv_status launch_shadow(nv_ctx *c);

@@ -97,7 +97,7 @@ EXPORTS = {
     "nv_hash_indices": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "nv_encode": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "nv_infer": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
-    "nv_backward": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "nv_backward": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "nv_optimizer_step": ([C.c_void_p], C.c_int),
     "nv_sample": ([C.POINTER(Volume), C.c_int64, C.c_uint64, C.c_uint32, C.c_void_p, C.c_void_p,
                    C.c_void_p], C.c_int),
@@ -320,10 +320,15 @@ class NeuralVolume:
         _check(lib().nv_infer(self._h, p, n, _dev(out, name="out")))
         return out
 
-    def backward(self, xyz, dy, dparams=None):
+    def backward(self, xyz, dy, dparams=None, dxyz=None):
+        """Adds the parameter gradient into dparams (None: the context's gradient
+        buffer); writes dL/dx of every point into dxyz ([n][3] float32) if given."""
         p, n = _points(xyz)
         dp = _dev(dparams, name="dparams") if dparams is not None else C.c_void_p()
-        _check(lib().nv_backward(self._h, p, n, _dev(dy.contiguous(), name="dL_dy"), dp))
+        dx = _dev(dxyz, name="dxyz") if dxyz is not None else C.c_void_p()
+        if dxyz is not None and dxyz.numel() != 3 * n:
+            raise ValueError("dxyz must hold n x 3 floats")
+        _check(lib().nv_backward(self._h, p, n, _dev(dy.contiguous(), name="dL_dy"), dp, dx))
 
     def optimizer_step(self):
         _check(lib().nv_optimizer_step(self._h))
@@ -585,7 +590,8 @@ class NeuralVolumeFunction(torch.autograd.Function):
     `params` is net.parameter(): a leaf tensor viewing the network's FP32
     parameters.  The forward calls nv_infer; the backward calls nv_backward,
     which recomputes the forward (nothing is stored in between) and returns
-    the parameter gradient, so torch accumulates it into params.grad."""
+    the parameter gradient, so torch accumulates it into params.grad, and the
+    gradient in the points when xyz requires one."""
 
     @staticmethod
     def forward(ctx, xyz, params, net: NeuralVolume):
@@ -597,5 +603,6 @@ class NeuralVolumeFunction(torch.autograd.Function):
     def backward(ctx, dy):
         (xyz,) = ctx.saved_tensors
         g = torch.zeros(ctx.net.n_params, dtype=torch.float32, device=dy.device)
-        ctx.net.backward(xyz.detach().contiguous(), dy.contiguous().float(), g)
-        return None, g, None
+        gx = torch.empty_like(xyz, dtype=torch.float32) if ctx.needs_input_grad[0] else None
+        ctx.net.backward(xyz.detach().contiguous(), dy.contiguous().float(), g, gx)
+        return gx, g, None
