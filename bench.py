@@ -558,7 +558,34 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
                                        "samples_per_frame": ad_ns, "iterations": ad_it, "image_psnr_db": ad_psnr},
                      "single_shot_shadows": {"frame_ms": sh_ms, "samples_per_frame": sh_ns, "iterations": sh_it},
                      "path_tracing_1spp": out_pt}
+        if prec == "fp16":
+            # samples per ray and iteration (Fig. 13's K): the image does not depend on K
+            sweep = {}
+            for k in (1, 2, 4, 8, 16):
+                rk = nv.Renderer(W * H, K=k)
+                img_k, ms_k = _time_render(rk, torch, frames, cam=cam, lut=lut, opts=dict(opts, K=k), net=net, mc=mc)
+                it_k, ns_k = rk.stats()
+                sweep[str(k)] = {"frame_ms": ms_k, "iterations": it_k, "samples_per_frame": ns_k,
+                                 "max_abs_diff_vs_k%d" % cfg["K"]: float((img_k - img).abs().max().item())}
+                rk.close()
+            out["k_sweep_fp16"] = sweep
         net.close()
+    # frame time and quality against the table size (Fig. 12's log2 T), FP16, same recipe
+    t_sweep = {}
+    for log2T in (17, 19, 21):
+        kw = dict(c.kwargs(), log2T=log2T)
+        net = nv.NeuralVolume(prec="fp16", **kw)
+        net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
+        for i in range(steps):
+            net.train_step(n=cfg["batch"], vol=vt, seed=11)
+        img, ms = _time_render(r, torch, frames, cam=cam, lut=lut, opts=opts, net=net, mc=mc)
+        it, ns = r.stats()
+        t_sweep[str(log2T)] = {"n_params": net.n_params, "compression_ratio": D ** 3 / net.n_params,
+                               "frame_ms": ms, "samples_per_frame": ns,
+                               "image_psnr_db": _psnr(nv.image_mse(img, raw).item()),
+                               "volume_psnr_db": _psnr(net.volume_mse(vt).item())}
+        net.close()
+    out["log2T_sweep_fp16"] = t_sweep
     r.close()
     del vt
     torch.cuda.empty_cache()
