@@ -196,8 +196,10 @@ nv_status nv_optimizer_step(nv_ctx *ctx);
 nv_status nv_sample(const nv_volume *vol, int64_t n, uint64_t seed, uint32_t step, float *xyz_dev,
                     float *target_dev, void *stream);
 /* One training step (Sec. 4): forward, the loss chosen by nv_set_loss
- * (default L2, mean((y - t)^2)), backward, Adam.  Either xyz_any/target_any hold the batch (host or device; host
- * batches are copied in on the context stream) or both are NULL and the batch
+ * (default L2, mean((y - t)^2)), backward, Adam.  Either xyz_any/target_any hold the batch (host or device; a
+ * host batch is copied on the context's own copy stream into one of two device staging slots, so the copy
+ * overlaps the previous step's kernels; the host memory must stay unchanged until this step has completed,
+ * e.g. until nv_sync) or both are NULL and the batch
  * is sampled from vol with nv_sample's generator at the context's sample
  * counter.  loss_dev (nullable): the batch loss before the update, FP64. */
 nv_status nv_train_step(nv_ctx *ctx, const float *xyz_any, const float *target_any, int64_t n,

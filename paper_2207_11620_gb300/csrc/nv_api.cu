@@ -84,7 +84,13 @@ static void ctx_free(nv_ctx *c) {
   cudaFree(c->adam_v);
   cudaFree(c->shadow);
   cudaFree(c->ds);
-  cudaFree(c->batch);
+  cudaFree(c->batch[0]);
+  cudaFree(c->batch[1]);
+  for (int b = 0; b < 2; ++b) {
+    if (c->batch_copied[b]) cudaEventDestroy(c->batch_copied[b]);
+    if (c->batch_used[b]) cudaEventDestroy(c->batch_used[b]);
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   cudaFree(c->tc_feat);
   cudaFree(c->tc_tgt);
   cudaFree(c->tc_xyz);
@@ -393,18 +399,40 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
   a.ds = c->ds;
   a.inv_n = (float)(1.0 / (double)n);
   a.l1 = c->loss_kind == NV_LOSS_L1;
+  int used_slot = -1;  // staging slot of a host batch
   if (xyz) {
     if (is_host_ptr(xyz) || is_host_ptr(target)) {
+      // host batch: copied on a copy stream into one of two staging slots, so
+      // this copy overlaps the previous step's kernels; the slot is reused only
+      // after the step that read it has finished
+      if (!c->copy_stream) {
+        NV_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "nv_train_step: copy stream");
+        for (int b = 0; b < 2; ++b) {
+          NV_CUDA(cudaEventCreateWithFlags(&c->batch_copied[b], cudaEventDisableTiming), "nv_train_step: event");
+          NV_CUDA(cudaEventCreateWithFlags(&c->batch_used[b], cudaEventDisableTiming), "nv_train_step: event");
+        }
+      }
       if (c->batch_cap < n) {
-        cudaFree(c->batch);
-        c->batch = nullptr;
+        NV_CUDA(cudaStreamSynchronize(c->copy_stream), "nv_train_step: staging");
+        NV_CUDA(cudaStreamSynchronize(c->stream), "nv_train_step: staging");
+        for (int b = 0; b < 2; ++b) {
+          cudaFree(c->batch[b]);
+          c->batch[b] = nullptr;
+        }
         c->batch_cap = 0;
-        NV_CUDA(cudaMalloc(&c->batch, (size_t)n * 4 * sizeof(float)), "nv_train_step: staging");
+        for (int b = 0; b < 2; ++b)
+          NV_CUDA(cudaMalloc(&c->batch[b], (size_t)n * 4 * sizeof(float)), "nv_train_step: staging");
         c->batch_cap = n;
       }
-      float *bx = c->batch, *bt = c->batch + 3 * n;
-      NV_CUDA(cudaMemcpyAsync(bx, xyz, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, c->stream), "H2D xyz");
-      NV_CUDA(cudaMemcpyAsync(bt, target, (size_t)n * sizeof(float), cudaMemcpyDefault, c->stream), "H2D target");
+      const int b = c->batch_slot;
+      c->batch_slot ^= 1;
+      float *bx = c->batch[b], *bt = c->batch[b] + 3 * n;
+      NV_CUDA(cudaStreamWaitEvent(c->copy_stream, c->batch_used[b], 0), "nv_train_step: wait");
+      NV_CUDA(cudaMemcpyAsync(bx, xyz, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, c->copy_stream), "H2D xyz");
+      NV_CUDA(cudaMemcpyAsync(bt, target, (size_t)n * sizeof(float), cudaMemcpyDefault, c->copy_stream), "H2D target");
+      NV_CUDA(cudaEventRecord(c->batch_copied[b], c->copy_stream), "nv_train_step: record");
+      NV_CUDA(cudaStreamWaitEvent(c->stream, c->batch_copied[b], 0), "nv_train_step: wait");
+      used_slot = b;
       a.xyz = bx;
       a.in = bt;
     } else {
@@ -433,6 +461,7 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
   int tk = prof_begin(c);
   NV_TRY(launch_adam(c, 1.0 / (double)n, loss_dev));
   prof_end(c, NV_K_ADAM, tk);
+  if (used_slot >= 0) NV_CUDA(cudaEventRecord(c->batch_used[used_slot], c->stream), "nv_train_step: record");
   return NV_OK;
 }
 

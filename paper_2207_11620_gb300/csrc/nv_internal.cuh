@@ -54,8 +54,11 @@ struct nv_ctx {
   int mc_nx, mc_ny, mc_nz, mc_cell;
   uint32_t sample_counter;                  // Philox step word of sampled batches
   int params_set;
-  float *batch;                             // staging for host batches: [cap][3] xyz + [cap] target
+  float *batch[2];                          // staging for host batches, two slots: [cap][3] xyz + [cap] target
   int64_t batch_cap;
+  int batch_slot;                           // slot of the next host batch
+  cudaStream_t copy_stream;                 // host-batch copies (created on first use)
+  cudaEvent_t batch_copied[2], batch_used[2];
   int num_sms;
   struct Prof *prof;                        // kernel timing (nv_profile_enable), NULL when off
   uint8_t *tc_feat;                         // tensor-core path: one chunk of 16-bit features (tile layout)
