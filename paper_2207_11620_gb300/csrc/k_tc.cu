@@ -119,6 +119,63 @@ __device__ __forceinline__ uint64_t desc_mn(uint32_t saddr, int Kphys) {  // MN-
   return kMnLboIsMn ? tc::smem_desc(saddr, mn, kk) : tc::smem_desc(saddr, kk, mn);
 }
 
+constexpr int kHotR = 16;  // dense replicas of the coarsest levels' gradient
+
+// Fold the dense replicas into the hashed table gradient, after the kernel
+// that scattered into them: one thread per vertex of the replicated levels
+// sums the R copies (in copy order), clears them and adds the sum to the
+// vertex's hash slot.
+__global__ void __launch_bounds__(256) k_fold_replicas(const __grid_constant__ NetDesc nd, const __grid_constant__ HotRep h,
+                                                       float *grads) {
+  const int F = nd.F;
+  const int64_t vtot = h.vbase[h.levels];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < vtot; v += (int64_t)gridDim.x * blockDim.x) {
+    int l = 0;
+    while (l + 1 < h.levels && v >= h.vbase[l + 1]) ++l;
+    const int n1 = h.n1[l];
+    const int64_t loc = v - h.vbase[l];
+    const int x = (int)(loc % n1), y = (int)((loc / n1) % n1), z = (int)(loc / ((int64_t)n1 * n1));
+    const int lim = nd.res[l] + 1;  // corners of cells of [0,1]^3 reach N_l + 1
+    if (x > lim || y > lim || z > lim) continue;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    bool any = false;
+    if (F == 2) {
+      float2 t[kHotR];
+#pragma unroll
+      for (int r = 0; r < kHotR; ++r) t[r] = __ldcg(reinterpret_cast<const float2 *>(h.buf + ((int64_t)r * vtot + v) * 2));
+#pragma unroll
+      for (int r = 0; r < kHotR; ++r) {
+        if (t[r].x != 0.f || t[r].y != 0.f) {
+          s[0] += t[r].x;
+          s[1] += t[r].y;
+          any = true;
+          *reinterpret_cast<float2 *>(h.buf + ((int64_t)r * vtot + v) * 2) = make_float2(0.f, 0.f);
+        }
+      }
+    } else {
+      float4 t[kHotR];
+#pragma unroll
+      for (int r = 0; r < kHotR; ++r) t[r] = __ldcg(reinterpret_cast<const float4 *>(h.buf + ((int64_t)r * vtot + v) * 4));
+#pragma unroll
+      for (int r = 0; r < kHotR; ++r) {
+        if (t[r].x != 0.f || t[r].y != 0.f || t[r].z != 0.f || t[r].w != 0.f) {
+          s[0] += t[r].x;
+          s[1] += t[r].y;
+          s[2] += t[r].z;
+          s[3] += t[r].w;
+          any = true;
+          *reinterpret_cast<float4 *>(h.buf + ((int64_t)r * vtot + v) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+    }
+    if (!any) continue;
+    const uint32_t hs = nv_hash3((uint32_t)x, (uint32_t)y, (uint32_t)z) & (nd.T - 1);
+    float *g = grads + ((size_t)l * nd.T + hs) * F;
+    if (F == 2) red_v2(g, s[0], s[1]);
+    else red_v4(g, s[0], s[1], s[2], s[3]);
+  }
+}
+
 // MODE_INFER: y = sigmoid(MLP(f)).  MODE 3: accumulate (y - vol)^2 into acc.
 // MODE_TRAIN: loss += (y - t)^2, dF = d(loss / n)/df.  MODE_BACKWARD: dF = dL/dy * dy/df.
 // TRAIN / BACKWARD add the weight gradients and the table gradient w_corner * dF
@@ -424,19 +481,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_mlp_tc(NetDesc nd, const float 
           for (int i = 0; i < DH; i += 4) dst[i / 4] = make_float4(df[i], df[i + 1], df[i + 2], df[i + 3]);
         }
         const float3 x = point_at(ps, p);
+        // the coarsest levels (all in half 0) go to this CTA's dense replica
+        const bool dense = hh == 0 && a.hot.levels > 0 && x.x >= 0.f && x.x <= 1.f && x.y >= 0.f && x.y <= 1.f &&
+                           x.z >= 0.f && x.z <= 1.f;
+        const int64_t rep_off = dense ? (int64_t)(blockIdx.x % a.hot.R) * a.hot.vbase[a.hot.levels] : 0;
         if (nd.F == 2) {
 #pragma unroll
           for (int k = 0; k < DH / 2; ++k) {
             const int l = hh * (DH / 2) + k;
-            scatter_level<2>(a.grads + (size_t)l * nd.T * 2, nd.T - 1, (float)nd.res[l], x.x, x.y, x.z,
-                             df + 2 * k);
+            if (k < 4 && dense && k < a.hot.levels)
+              scatter_dense<2>(a.hot.buf + (rep_off + a.hot.vbase[k < 4 ? k : 0]) * 2, a.hot.n1[k < 4 ? k : 0],
+                               (float)nd.res[l], x.x, x.y, x.z, df + 2 * k);
+            else
+              scatter_level<2>(a.grads + (size_t)l * nd.T * 2, nd.T - 1, (float)nd.res[l], x.x, x.y, x.z,
+                               df + 2 * k);
           }
         } else {
 #pragma unroll
           for (int k = 0; k < DH / 4; ++k) {
             const int l = hh * (DH / 4) + k;
-            scatter_level<4>(a.grads + (size_t)l * nd.T * 4, nd.T - 1, (float)nd.res[l], x.x, x.y, x.z,
-                             df + 4 * k);
+            if (k < 4 && dense && k < a.hot.levels)
+              scatter_dense<4>(a.hot.buf + (rep_off + a.hot.vbase[k < 4 ? k : 0]) * 4, a.hot.n1[k < 4 ? k : 0],
+                               (float)nd.res[l], x.x, x.y, x.z, df + 4 * k);
+            else
+              scatter_level<4>(a.grads + (size_t)l * nd.T * 4, nd.T - 1, (float)nd.res[l], x.x, x.y, x.z,
+                               df + 4 * k);
           }
         }
       }
@@ -616,6 +685,8 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
     ps.seed = a.seed;
     ps.step = a.sample_step;
   }
+  MlpArgs am = a;  // the MLP kernel's arguments: backward passes scatter the coarsest levels into replicas
+  if (mode == MODE_TRAIN || mode == MODE_BACKWARD) am.hot = c->hot;
   // a sampled training batch: the gather kernel computes each Philox point
   // once for the MLP kernel too (its points and targets)
   const bool sampled = mode == MODE_TRAIN && ps.kind == 2;
@@ -637,8 +708,13 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
       pm.xyz = c->tc_xyz;
       pm.xyz_off = off;
     }
-    s = c->prec == NV_BF16 ? dispatch_shape<true>(c, mode, a, pm, cs, c->tc_feat, tgt, acc)
-                           : dispatch_shape<false>(c, mode, a, pm, cs, c->tc_feat, tgt, acc);
+    s = c->prec == NV_BF16 ? dispatch_shape<true>(c, mode, am, pm, cs, c->tc_feat, tgt, acc)
+                           : dispatch_shape<false>(c, mode, am, pm, cs, c->tc_feat, tgt, acc);
+    if (s == NV_OK && am.hot.levels > 0) {
+      const int64_t vtot = am.hot.vbase[am.hot.levels];
+      k_fold_replicas<<<(unsigned)((vtot + 255) / 256), 256, 0, c->stream>>>(c->nd, am.hot, am.grads);
+      s = nv_cuda_check(cudaGetLastError(), "k_fold_replicas launch");
+    }
     prof_end(c, NV_K_MLP, tk);
     if (s != NV_OK) return s;
   }
@@ -647,4 +723,34 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
 
 nv_status launch_mlp_tc(const nv_ctx *c, int mode, const MlpArgs &a) {
   return launch_mlp_tc_ext(c, mode, a, nullptr, 1, a.n, mode == MODE_TRAIN ? &a.ds->loss_acc : nullptr);
+}
+
+// Dense replicas of the coarsest levels' table gradient: consecutive levels
+// from 0 whose padded vertex grid holds at most 2^15 vertices (at most four,
+// all in the first half of the levels), 16 copies.
+nv_status build_hot_replicas(nv_ctx *c) {
+  HotRep h{};
+  const NetDesc &nd = c->nd;
+  int64_t v = 0;
+  for (int l = 0; l < 4 && l < nd.L / 2; ++l) {
+    const int n1 = (nd.res[l] + 3) & ~1;
+    if ((int64_t)n1 * n1 * n1 > 32768) break;
+    h.n1[l] = n1;
+    h.vbase[l] = v;
+    v += (int64_t)n1 * n1 * n1;
+    h.levels = l + 1;
+  }
+  h.vbase[h.levels] = v;
+  h.R = kHotR;
+  c->hot = HotRep{};
+  if (h.levels == 0 || c->prec == NV_FP32 || !tc_supported(nd)) return NV_OK;
+  cudaError_t e = cudaMalloc(&h.buf, (size_t)h.R * v * nd.F * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h.buf, 0, (size_t)h.R * v * nd.F * sizeof(float), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(h.buf);
+    return nv_cuda_check(e, "replicas of the coarse levels' gradient");
+  }
+  c->hot = h;
+  return NV_OK;
 }

@@ -96,6 +96,7 @@ static void ctx_free(nv_ctx *c) {
   cudaFree(c->tc_xyz);
   cudaFree(c->adam_blocks);
   cudaFree(c->df_buf);
+  cudaFree(c->hot.buf);
   delete c;
 }
 
@@ -180,6 +181,7 @@ extern "C" nv_status nv_create(int L, int F, int log2T, int Nmin, double b, cons
     return s;
   }
   nv_status sb = build_adam_blocks(c);
+  if (sb == NV_OK) sb = build_hot_replicas(c);
   if (sb != NV_OK) {
     ctx_free(c);
     return sb;

@@ -38,6 +38,19 @@ struct DevState {
   int off_domain;     // set (for good) when a table gradient was scattered from a point outside [0,1]^3
 };
 
+// Dense replicas of the coarsest levels' table gradient (tensor-core
+// training): level l < levels keeps R copies of an n1[l]^3-vertex grid (n1 =
+// N_l + 2 rounded up to even, x fastest), F floats per vertex; the backward
+// scatters a point of [0,1]^3 into copy (CTA mod R) by vertex index; a
+// following kernel folds the copies into the hashed slots.
+struct HotRep {
+  float *buf;          // [R][vtot][F], zero between launches
+  int levels;          // 0: no replicas
+  int R;
+  int n1[4];
+  int64_t vbase[5];    // first vertex of each level; vbase[levels] = vtot
+};
+
 struct nv_ctx {
   NetDesc nd;
   int Nmin;
@@ -70,6 +83,7 @@ struct nv_ctx {
   int adam_dense;                           // 1: Adam visits every block from now on (sticky)
   float *df_buf;                            // nv_backward with a coordinate gradient: dL/df [cap][L*F]
   int64_t df_cap;
+  HotRep hot;                               // dense replicas of the coarsest levels' gradient (TC path)
 };
 
 // Kernel timing hooks (nv_api.cu): bracket a launch on the context stream.
@@ -261,6 +275,7 @@ struct MlpArgs {
   float inv_n;           // TRAIN: 1/n of the batch mean
   int l1;                // TRAIN: L1 loss (else L2)
   float *df_out;         // BACKWARD (nullable): dL/df of every point, [n][L*F] FP32
+  HotRep hot;            // TRAIN / BACKWARD, tensor-core path (levels = 0: none)
 };
 
 // FP32 CUDA-core path
@@ -282,6 +297,7 @@ bool tc_supported(const NetDesc &nd);
 nv_status launch_adam(nv_ctx *c, double inv_n, double *loss_out);
 nv_status launch_coord_grad(const nv_ctx *c, const float *xyz, int64_t n, const float *df, float *dxyz);
 nv_status build_adam_blocks(nv_ctx *c);
+nv_status build_hot_replicas(nv_ctx *c);
 nv_status launch_scale_double(double *x, double s, cudaStream_t st);
 nv_status launch_shadow(nv_ctx *c);
 // sampling, macrocells, rendering, reductions

@@ -300,6 +300,40 @@ __device__ __forceinline__ void red_entry(float *p, const float *g) {
   }
 }
 
+// A-7 at one level into a dense vertex grid (x fastest, n1 even): the two
+// x-corners of an even cell are adjacent and 16-byte aligned at F = 2, one
+// vector reduction; otherwise one per corner.  Only for points of [0,1]^3
+// (corners 0..N+1 < n1).
+template <int F>
+__device__ __forceinline__ void scatter_dense(float *rep, int n1, float N, float x, float y, float z,
+                                              const float *df) {
+  int cx, cy, cz;
+  float wx, wy, wz;
+  nv_cell(x, N, cx, wx);
+  nv_cell(y, N, cy, wy);
+  nv_cell(z, N, cz, wz);
+  const bool even = (cx & 1) == 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int dy = q & 1, dz = q >> 1;
+    const float wyz = (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
+    const float w0 = (1.f - wx) * wyz, w1 = wx * wyz;
+    float g0[F], g1[F];
+#pragma unroll
+    for (int j = 0; j < F; ++j) {
+      g0[j] = w0 * df[j];
+      g1[j] = w1 * df[j];
+    }
+    float *dst = rep + (((int64_t)(cz + dz) * n1 + (cy + dy)) * n1 + cx) * F;
+    if (F == 2 && even) {
+      red_v4(dst, g0[0], g0[1], g1[0], g1[1]);
+    } else {
+      red_entry<F>(dst, g0);
+      red_entry<F>(dst + F, g1);
+    }
+  }
+}
+
 // A-7 for one level, x-paired like the gather: for even cx and F = 2 both
 // x-corners land in one 16-byte aligned pair of FP32 entries and take one
 // vector atomic.
