@@ -401,7 +401,8 @@ typedef enum {
   NV_K_RENDER = 3,
   NV_K_OTHER = 4,
   NV_K_ENCODE = 5,  /* tensor-core path: hash gather into feature tiles */
-  NV_K_SCATTER = 6  /* no launches: the tensor-core path scatters inside the MLP kernel */
+  NV_K_SCATTER = 6  /* tensor-core training: the fold of the coarsest levels' gradient replicas into the hashed
+                      slots (the scatter itself runs inside the MLP kernel) */
 } nv_kclass;
 nv_status nv_profile_enable(nv_ctx *ctx, int enable);
 nv_status nv_profile_read(nv_ctx *ctx, int kclass, double *total_ms, int *launches);

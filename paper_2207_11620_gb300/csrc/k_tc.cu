@@ -119,7 +119,7 @@ __device__ __forceinline__ uint64_t desc_mn(uint32_t saddr, int Kphys) {  // MN-
   return kMnLboIsMn ? tc::smem_desc(saddr, mn, kk) : tc::smem_desc(saddr, kk, mn);
 }
 
-constexpr int kHotR = 16;  // dense replicas of the coarsest levels' gradient
+constexpr int kHotR = 8;  // dense replicas of the coarsest levels' gradient
 
 // Fold the dense replicas into the hashed table gradient, after the kernel
 // that scattered into them: one thread per vertex of the replicated levels
@@ -710,13 +710,16 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
     }
     s = c->prec == NV_BF16 ? dispatch_shape<true>(c, mode, am, pm, cs, c->tc_feat, tgt, acc)
                            : dispatch_shape<false>(c, mode, am, pm, cs, c->tc_feat, tgt, acc);
-    if (s == NV_OK && am.hot.levels > 0) {
+    prof_end(c, NV_K_MLP, tk);
+    if (s != NV_OK) return s;
+    if (am.hot.levels > 0) {
+      tk = prof_begin(c);
       const int64_t vtot = am.hot.vbase[am.hot.levels];
       k_fold_replicas<<<(unsigned)((vtot + 255) / 256), 256, 0, c->stream>>>(c->nd, am.hot, am.grads);
       s = nv_cuda_check(cudaGetLastError(), "k_fold_replicas launch");
+      prof_end(c, NV_K_SCATTER, tk);
+      if (s != NV_OK) return s;
     }
-    prof_end(c, NV_K_MLP, tk);
-    if (s != NV_OK) return s;
   }
   return NV_OK;
 }
@@ -727,7 +730,7 @@ nv_status launch_mlp_tc(const nv_ctx *c, int mode, const MlpArgs &a) {
 
 // Dense replicas of the coarsest levels' table gradient: consecutive levels
 // from 0 whose padded vertex grid holds at most 2^15 vertices (at most four,
-// all in the first half of the levels), 16 copies.
+// all in the first half of the levels), kHotR copies.
 nv_status build_hot_replicas(nv_ctx *c) {
   HotRep h{};
   const NetDesc &nd = c->nd;
