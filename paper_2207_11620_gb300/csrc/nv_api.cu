@@ -192,6 +192,7 @@ extern "C" nv_status nv_create(int L, int F, int log2T, int Nmin, double b, cons
 
 extern "C" nv_status nv_destroy(nv_ctx *c) {
   if (!c) return NV_OK;
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   cudaStreamSynchronize(c->stream);
   ctx_free(c);
   return NV_OK;
