@@ -143,6 +143,32 @@ def test_tc_train_step_cfg2_full_size(nv, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tc_backward_over_several_chunks(nv, prec):
+    """More points than one chunk of the tensor-core path (2^19): each chunk's
+    kernel scatters the coarsest levels into the dense replicas and a fold
+    follows it, so the replicas must come back to zero between chunks.  Config
+    1's shape keeps the serial oracle within seconds."""
+    c = CF.CFG1_NET
+    net = nv.NeuralVolume(prec=prec, **c.kwargs())
+    params = I.uniform_params(net.n_params, seed=47, scale=0.5)
+    net.set_params(params)
+    n = (1 << 19) + 2 * 128 + 5  # two chunks and a ragged tail
+    x = I.uniform_points(n, seed=48)
+    dy = np.random.default_rng(49).uniform(0.5, 1.5, size=n).astype(np.float32) / n
+    g = torch.zeros(net.n_params, dtype=torch.float32, device="cuda")
+    xt, dt = torch.from_numpy(x).cuda(), torch.from_numpy(dy).cuda()
+    net.backward(xt, dt, g)
+    want = O.backward(onet(c), params, x, dy.astype(np.float64))
+    got = g.cpu().numpy()
+    nt = net.n_table
+    assert norm_rel(got[nt:], want[nt:]) <= GRAD_TOL[prec], norm_rel(got[nt:], want[nt:])
+    assert norm_rel(got[:nt], want[:nt]) <= TABLE_TOL[prec], norm_rel(got[:nt], want[:nt])
+    # a second call adds the same gradient again: nothing was left in the replicas
+    net.backward(xt, dt, g)
+    assert norm_rel(g.cpu().numpy() - got, want) <= TABLE_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_tc_training_converges_like_fp32(nv, prec):
     c = CF.CFG2_NET
     vol = torch.from_numpy(I.blob_volume(32, seed=3)).cuda()
