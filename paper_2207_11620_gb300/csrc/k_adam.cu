@@ -3,7 +3,7 @@
 // Per parameter the kernel reads p, g, m, v (16 B) and writes p, m, v, g = 0
 // (16 B) plus the FP16/BF16 shadow (2 B) in tensor-core precisions: 32-34 B of
 // algorithmic traffic per parameter, in blocks of 128 parameters (512 B of
-// each array).  Persistent CTAs (as many as fit, two per SM) stream tiles of kCW blocks
+// each array).  Persistent CTAs (as many as fit: three per SM) stream tiles of kCW blocks
 // through a kStages-deep shared-memory ring: one producer warp brings p, g, m
 // and v of a tile in with bulk asynchronous copies (the copy engine; runs of
 // consecutive blocks in one copy per array) counted on an mbarrier, and each of
@@ -46,7 +46,7 @@ struct AdamHP {
 
 constexpr int kBlk = 32;                              // float4 groups per block: 128 parameters, one per lane
 constexpr int kCW = 8;                                // consumer warps = blocks per tile
-constexpr int kStages = 6;                            // tiles in flight per CTA
+constexpr int kStages = 4;                            // tiles in flight per CTA
 constexpr int kAdamThreads = (kCW + 1) * 32;          // + the producer warp
 constexpr int kStageF4 = 4 * kCW * kBlk;              // float4 of p, g, m, v of one tile (16 KB)
 constexpr size_t kAdamSmem = (size_t)kStages * kStageF4 * 16 + 2 * kStages * 8 + kStages * kCW * 8;
