@@ -24,7 +24,7 @@
 // list is built once per network; Adam falls back to every block, for good,
 // once that premise may fail: an L2 term, a gradient or moment buffer handed
 // to the caller, or a gradient scattered from a point outside [0,1]^3 (the
-// scatter kernels set a device flag).
+// kernels that read given training points set a device flag).
 //
 // The step counter, the overflow flag and the loss scale live on the device,
 // so a step whose gradient overflowed is skipped without a host round trip
