@@ -580,27 +580,28 @@ nv_status launch_mlp(const nv_ctx *c, const MlpArgs &a, const PointSrc &ps, cons
   const size_t min_bytes = 233472 / (tmem_cap + 1) + 1024;
   if (bytes < min_bytes) bytes = min_bytes;
   auto kern = k_mlp_tc<D0, BF, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(k_mlp_tc)");
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(carveout)");
-  // resident CTAs per SM: the tightest of registers, shared memory and tensor memory
-  static int regs_sm = 0, smem_sm = 0, smem_rsv = 0;
-  if (!regs_sm) {
-    int dev = 0;
+  // set up once per kernel instance (device attributes of the first device used)
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(k_mlp_tc)");
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(carveout)");
+    // resident CTAs per SM: the tightest of registers, shared memory and tensor memory
+    int dev = 0, regs_sm = 0, smem_sm = 0, smem_rsv = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncGetAttributes(k_mlp_tc)");
+    const int by_regs = regs_sm / (((fa.numRegs + 7) & ~7) * kThreads);
+    const int by_smem = smem_sm / (int)(bytes + smem_rsv);
+    int n = by_regs < by_smem ? by_regs : by_smem;
+    if (n > tmem_cap) n = tmem_cap;
+    per_sm = n < 1 ? 1 : n;
   }
-  cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, kern);
-  if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncGetAttributes(k_mlp_tc)");
-  const int by_regs = regs_sm / (((fa.numRegs + 7) & ~7) * kThreads);
-  const int by_smem = smem_sm / (int)(bytes + smem_rsv);
-  int per_sm = by_regs < by_smem ? by_regs : by_smem;
-  if (per_sm > tmem_cap) per_sm = tmem_cap;
-  if (per_sm < 1) per_sm = 1;
   const int64_t ntiles = (cs.cap + kTP - 1) / kTP;
   int64_t grid = (int64_t)c->num_sms * per_sm;
   if (ntiles < grid) grid = ntiles;
