@@ -36,6 +36,27 @@ def test_library_exports_every_declared_symbol(nvmod):
     assert set(_declared()) == set(nvmod.EXPORTS)
 
 
+def _prototypes():
+    """name -> number of parameters of every entry point declared in nv.h."""
+    txt = open(os.path.join(ROOT, "include", "nv.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"(?:nv_status|const char \*)\s*(nv_\w+)\s*\(([^;{]*?)\)\s*;", txt, re.S):
+        args = " ".join(m.group(2).split())
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(nvmod):
+    """The ctypes table of the binding has one argument type per declared
+    parameter, so a changed signature cannot be marshalled with a stale one."""
+    protos = _prototypes()
+    table = nvmod.EXPORTS
+    assert set(protos) == set(table)
+    bad = {n: (protos[n], len(table[n][0])) for n in protos if protos[n] != len(table[n][0])}
+    assert not bad, bad
+
+
 def _create(nvmod, L=8, F=2, log2T=14, Nmin=16, b=1.5, dims=(16, 64, 64, 1), prec=0):
     arr = (C.c_int * len(dims))(*dims)
     h = C.c_void_p()
