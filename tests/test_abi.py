@@ -57,6 +57,21 @@ def test_binding_argument_counts_match_the_header(nvmod):
     assert not bad, bad
 
 
+def _enum_values():
+    """NAME -> value of every enumerator in nv.h (explicit values only)."""
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "nv.h")).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(NV_[A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+
+
+def test_binding_constants_match_the_header_enums(nvmod):
+    ev = _enum_values()
+    assert nvmod.PREC == {"fp32": ev["NV_FP32"], "fp16": ev["NV_FP16"], "bf16": ev["NV_BF16"]}
+    assert nvmod.BUF == {"params": ev["NV_BUF_PARAMS"], "grads": ev["NV_BUF_GRADS"],
+                         "adam_m": ev["NV_BUF_ADAM_M"], "adam_v": ev["NV_BUF_ADAM_V"]}
+    for name, v in nvmod.KCLASS.items():
+        assert ev["NV_K_" + name.upper()] == v, name
+
+
 def _create(nvmod, L=8, F=2, log2T=14, Nmin=16, b=1.5, dims=(16, 64, 64, 1), prec=0):
     arr = (C.c_int * len(dims))(*dims)
     h = C.c_void_p()
