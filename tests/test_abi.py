@@ -72,6 +72,40 @@ def test_binding_constants_match_the_header_enums(nvmod):
         assert ev["NV_K_" + name.upper()] == v, name
 
 
+def test_binding_structs_have_the_header_layout():
+    """Every argument struct the binding builds has the C struct's size and
+    field offsets (a C program compiled against nv.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_2207_11620_gb300 import nv as binding
+    pairs = [(binding.Volume, "nv_volume"), (binding.Camera, "nv_camera"), (binding.RenderOpts, "nv_render_opts"),
+             (binding.PtOpts, "nv_pt_opts"), (binding.Macrocells, "nv_macrocells"),
+             (binding.AdamCfg, "nv_adam_cfg")]
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "nv.h"', "int main(void) {"]
+    for cls, cname in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    out_dir = os.path.join(ROOT, "tests", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    src, exe = os.path.join(out_dir, "layout.c"), os.path.join(out_dir, "layout")
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+    got = {}
+    for ln in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = ln.split()
+        got[(a, b)] = int(v)
+    for cls, cname in pairs:
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
 def _create(nvmod, L=8, F=2, log2T=14, Nmin=16, b=1.5, dims=(16, 64, 64, 1), prec=0):
     arr = (C.c_int * len(dims))(*dims)
     h = C.c_void_p()
