@@ -50,7 +50,7 @@ typedef enum {
   NV_ERR_CUDA = 3,        /* a CUDA call or launch failed */
   NV_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (kernel returned early) */
   NV_ERR_STATE = 5,       /* call out of order (e.g. params never set) */
-  NV_ERR_UNSUPPORTED = 6  /* shape or precision this build has no kernel for */
+  NV_ERR_UNSUPPORTED = 6  /* shape or precision the library has no kernel for */
 } nv_status;
 
 typedef enum {
