@@ -57,3 +57,27 @@ def expected_errors(net, params, xyz, dy, prec):
     exact = backward_model(net, params, xyz, dy, "exact")
     got = backward_model(net, params, xyz, dy, prec)
     return {name: normwise(g, e) for name, g, e in zip(("dF", "dW0", "dW1", "dW2"), got, exact)}
+
+
+def coord_grad_from_df(net: O.Net, params, xyz, dF):
+    """dL/dx of every point from a given dL/df: the Jacobian of the trilinear
+    encoding (within a cell of level l, d w_a / d x_a = N_l) applied to dF,
+    with the unrounded tables (the GPU applies it with its FP32 master tables)."""
+    xyz = np.asarray(xyz, np.float32)
+    p = np.asarray(params, np.float64)
+    idx = O.hash_indices(net, xyz).astype(np.int64)  # [n][L][8], corner d = dx + 2 dy + 4 dz
+    n, F, T = xyz.shape[0], net.F, net.T
+    g = np.zeros((n, 3))
+    for l, N in enumerate(net.res):
+        pc = xyz * np.float32(N)  # the kernel's single FP32 multiply
+        w = pc.astype(np.float64) - np.floor(pc.astype(np.float64))
+        df = dF[:, l * F:(l + 1) * F]
+        for d in range(8):
+            bits = (d & 1, (d >> 1) & 1, (d >> 2) & 1)
+            theta = p[(l * T + idx[:, l, d])[:, None] * F + np.arange(F)[None, :]]
+            dot = np.sum(theta * df, axis=1)
+            fac = [w[:, a] if bits[a] else 1.0 - w[:, a] for a in range(3)]
+            for a in range(3):
+                dw = (1.0 if bits[a] else -1.0) * fac[(a + 1) % 3] * fac[(a + 2) % 3]
+                g[:, a] += N * dw * dot
+    return g
