@@ -38,7 +38,7 @@ def reachable_blocks(L, F, log2T, res, n_params):
     on = np.zeros(nblk, bool)
     on[n_table // BLOCK:] = True  # any block holding a weight
     for l in range(L):
-        n1 = res[l] + 2
+        n1 = int(res[l]) + 2
         lo, hi = l * T * F, (l + 1) * T * F
         if n1 ** 3 > 4 * T:
             on[lo // BLOCK:(hi - 1) // BLOCK + 1] = True
