@@ -335,15 +335,20 @@ nv_status nv_render_pt(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const 
 nv_status nv_render_stats(nv_renderer *r, int *iterations, int64_t *samples);
 
 /* The paper has no counterpart to this entry point.  It is nv_render on the
- * raw volume (net = NULL) for callers that cannot allocate device memory: code
- * running while a CUDA graph is captured on its stream, real-time loops whose
- * memory is fixed up front, or plugins inside an application that owns every
- * allocation.  It calls no cudaMalloc, cudaFree, cudaMallocHost, event or
- * stream creation; ray buffers, sample batches and counters come from one
- * static device array of NV_NOALLOC_SCRATCH_BYTES (about 16 MB) that every GPU
- * loading the library holds until the process exits.
+ * raw volume (net = NULL) for callers that cannot allocate device memory:
+ * real-time loops whose memory is fixed up front (cudaMalloc and cudaFree may
+ * synchronise the device and take unbounded time, which a frame deadline
+ * cannot absorb), and plugins inside a host application that owns every
+ * allocation and budgets the GPU's memory itself.  It calls no cudaMalloc,
+ * cudaFree, cudaMallocHost, event or stream creation; ray buffers, sample
+ * batches and counters come from one static device array of
+ * NV_NOALLOC_SCRATCH_BYTES (about 16 MB) that every GPU loading the library
+ * holds until the process exits.
  *  - Images up to NV_NOALLOC_MAX_PIXELS pixels (256 x 256) and K up to
  *    NV_NOALLOC_MAX_K; larger requests fail with NV_ERR_ARG and a message.
+ *  - Only the fixed-step emission-absorption march: opts->step_max > 0
+ *    (adaptive step) or opts->shade != 0 (shadows) fail with
+ *    NV_ERR_UNSUPPORTED before anything is enqueued.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture.
@@ -352,7 +357,7 @@ nv_status nv_render_stats(nv_renderer *r, int *iterations, int64_t *samples);
  *    overlaps (other streams, other host threads) race on the same scratch.
  *  - The live-ray count is read back synchronously after every iteration, so
  *    the call returns when the image is complete.
- * Arguments as nv_render; mc may be NULL; stream NULL = legacy default stream. */
+ * Other arguments as nv_render; mc may be NULL; stream NULL = legacy default stream. */
 #define NV_NOALLOC_MAX_PIXELS 65536
 #define NV_NOALLOC_MAX_K 8
 #define NV_NOALLOC_SCRATCH_BYTES 15991296

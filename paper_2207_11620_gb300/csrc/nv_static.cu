@@ -2,13 +2,16 @@
 // that must not allocate device memory, with its scratch in a fixed static
 // device array instead of an nv_renderer.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured on its stream, real-time loops whose memory budget is fixed
-// up front, plugins inside a host application that owns every allocation, or
-// callers that would otherwise have to keep a renderer object alive just to
-// draw an occasional small image.  This entry point serves them: it allocates
-// nothing (no cudaMalloc, cudaFree, cudaMallocHost, event or stream creation)
-// and takes its ray buffers, sample batches and counters from the array below.
+// Some callers cannot call cudaMalloc: real-time loops whose memory budget is
+// fixed up front (an allocation may synchronise the device and take unbounded
+// time inside a frame), plugins inside a host application that owns every
+// allocation and budgets the GPU's memory itself, or callers that would
+// otherwise have to keep a renderer object alive just to draw an occasional
+// small image.  This entry point serves them: it allocates nothing (no
+// cudaMalloc, cudaFree, cudaMallocHost, event or stream creation) and takes
+// its ray buffers, sample batches and counters from the array below.  It runs
+// the fixed-step emission-absorption march only (no adaptive step, no
+// shadows).
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (NV_NOALLOC_SCRATCH_BYTES, about 16 MB) until the process
