@@ -283,23 +283,51 @@ static void or_point_df(int L, int F, int log2T, const int *res, const int *dims
 /* A-6 / A-7: analytic backward of encode + MLP for upstream gradients dL/dy.
  * Accumulates (+=) into grads, laid out like params (tables then weights):
  * the weight gradients of or_point_df, and for every corner of every level
- * its trilinear weight times df (the adjoint of A-3).  Serial: the scatter
- * into shared table entries is order dependent. */
+ * its trilinear weight times df (the adjoint of A-3).
+ * Threads: the per-point chain rule runs over points in parallel (df of every
+ * point kept, weight gradients summed per thread, then over the threads in
+ * order); the scatter runs over levels in parallel, each level visiting the
+ * points in order, so every table entry sums its contributions in point
+ * order, as a serial loop would. */
 void or_backward(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
                  const double *params, const float *xyz, int64_t n, const double *dL_dy,
                  double *grads) {
   uint32_t T = 1u << log2T;
   int64_t tab = (int64_t)L * T * F;
+  int64_t nw = or_weight_count(dims, n_dims);
   int alen = or_act_len(dims, n_dims);
   int mx = or_max_dim(dims, n_dims);
-  double *act = (double *)malloc(sizeof(double) * alen);
-  double *delta = (double *)malloc(sizeof(double) * mx);
-  double *din = (double *)malloc(sizeof(double) * mx);
-  for (int64_t i = 0; i < n; ++i) {
-    const float *x = xyz + 3 * i;
-    or_point_df(L, F, log2T, res, dims, n_dims, params, x, dL_dy[i], grads + tab, act, delta, din);
-    /* delta now holds df (length L*F): scatter into the table gradients */
-    for (int l = 0; l < L; ++l) {
+  int LF = L * F;
+  double *df = (double *)malloc(sizeof(double) * (n > 0 ? n : 1) * LF);
+  int nt = 1;
+#ifdef _OPENMP
+  nt = omp_get_max_threads();
+#endif
+  double *gw = (double *)calloc((size_t)nt * nw, sizeof(double));
+#pragma omp parallel num_threads(nt)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double *act = (double *)malloc(sizeof(double) * alen);
+    double *delta = (double *)malloc(sizeof(double) * mx);
+    double *din = (double *)malloc(sizeof(double) * mx);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      or_point_df(L, F, log2T, res, dims, n_dims, params, xyz + 3 * i, dL_dy[i], gw + (int64_t)tid * nw, act,
+                  delta, din);
+      memcpy(df + i * LF, delta, sizeof(double) * LF);  /* delta holds df (length L*F) */
+    }
+    free(act); free(delta); free(din);
+  }
+  for (int t = 0; t < nt; ++t)
+    for (int64_t k = 0; k < nw; ++k) grads[tab + k] += gw[(int64_t)t * nw + k];
+  /* the scatter into the table gradients, level by level */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int l = 0; l < L; ++l)
+    for (int64_t i = 0; i < n; ++i) {
+      const float *x = xyz + 3 * i;
       int64_t c[3]; double w[3];
       for (int a = 0; a < 3; ++a) or_cell(x[a], res[l], &c[a], &w[a]);
       for (int d = 0; d < 8; ++d) {
@@ -307,11 +335,10 @@ void or_backward(int L, int F, int log2T, const int *res, const int *dims, int n
         double wt = (dx ? w[0] : 1.0 - w[0]) * (dy ? w[1] : 1.0 - w[1]) * (dz ? w[2] : 1.0 - w[2]);
         uint32_t h = or_hash(c[0] + dx, c[1] + dy, c[2] + dz, T);
         double *g = grads + ((int64_t)l * T + h) * F;
-        for (int j = 0; j < F; ++j) g[j] += wt * delta[l * F + j];
+        for (int j = 0; j < F; ++j) g[j] += wt * df[i * LF + l * F + j];
       }
     }
-  }
-  free(act); free(delta); free(din);
+  free(df); free(gw);
 }
 
 /* Gradient of the loss with respect to the point coordinates: dxyz[i][a] =
@@ -360,12 +387,233 @@ void or_backward_x(int L, int F, int log2T, const int *res, const int *dims, int
   }
 }
 
+/* --------------------------------------------------- error magnitudes -- */
+
+/* Per-element error magnitudes for the parity bounds (test infrastructure).
+ * For a quantity q of the path, M(q) >= |q| is the magnitude its rounding
+ * errors scale with, propagated in FP64 by the rules of running error
+ * analysis (Wilkinson; Higham, "Accuracy and Stability of Numerical
+ * Algorithms", ch. 3): an exact input has M = |q|; a sum or a dot product has
+ * the sum of its terms' magnitudes (the Sum |terms| of the classical bound
+ * |fl(sum) - sum| <= gamma_n Sum |terms|), a product the product of its
+ * factors' magnitudes, and a smooth function g of z has |g(z)| + |g'(z)| M(z).
+ * An evaluation that rounds each operation to a unit roundoff u, in any order,
+ * with chains of at most k dependent roundings, stays within about k u M(q)
+ * of q; where nothing cancels, M(q) = |q| and the bound is relative.
+ *
+ * ReLU: the forward passes M unmasked (a unit whose sign the rounding decides
+ * moves its output by at most its own error, which M then still covers).  The
+ * backward's masks 1[z > 0] are discontinuous, so a backward magnitude holds
+ * only for points whose pre-activations are all clear of zero by more than
+ * their error (the kink margin or_forward_mag reports); with masked == 0 every
+ * unit is counted instead, a magnitude that covers any masks. */
+
+/* A-1..A-3 with magnitudes: f as or_encode_point, fm = Sum_corners w |theta|. */
+static void or_encode_point_mag(int L, int F, int log2T, const int *res, const double *tables,
+                                const float *x, double *f, double *fm) {
+  uint32_t T = 1u << log2T;
+  for (int l = 0; l < L; ++l) {
+    int64_t c[3]; double w[3];
+    for (int a = 0; a < 3; ++a) or_cell(x[a], res[l], &c[a], &w[a]);
+    for (int j = 0; j < F; ++j) { f[l * F + j] = 0.0; fm[l * F + j] = 0.0; }
+    for (int d = 0; d < 8; ++d) {
+      int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+      double wt = (dx ? w[0] : 1.0 - w[0]) * (dy ? w[1] : 1.0 - w[1]) * (dz ? w[2] : 1.0 - w[2]);
+      uint32_t h = or_hash(c[0] + dx, c[1] + dy, c[2] + dz, T);
+      const double *e = tables + ((int64_t)l * T + h) * F;
+      for (int j = 0; j < F; ++j) {
+        f[l * F + j] += wt * e[j];
+        fm[l * F + j] += wt * fabs(e[j]);
+      }
+    }
+  }
+}
+
+/* A-4 with magnitudes: act / actm hold every layer's values and magnitudes
+ * (layout of or_mlp_point, the input layer filled by the caller).  Returns y;
+ * *ymag = y + y (1 - y) M(z_out); *kink = the smallest |z| / M(z) over the
+ * hidden units (infinity if none has M(z) > 0). */
+static double or_mlp_point_mag(const int *dims, int n_dims, const double *weights, double *act, double *actm,
+                               double *ymag, double *kink) {
+  const double *W = weights;
+  double *a = act, *am = actm;
+  double z_out = 0.0, zm_out = 0.0, margin = INFINITY;
+  for (int k = 0; k + 1 < n_dims; ++k) {
+    int din = dims[k], dout = dims[k + 1];
+    double *an = a + din, *amn = am + din;
+    for (int j = 0; j < dout; ++j) {
+      double z = 0.0, zm = 0.0;
+      for (int i = 0; i < din; ++i) {
+        z += W[(int64_t)j * din + i] * a[i];
+        zm += fabs(W[(int64_t)j * din + i]) * am[i];
+      }
+      if (k + 2 < n_dims) {
+        an[j] = z > 0.0 ? z : 0.0;
+        amn[j] = zm;
+        if (zm > 0.0 && fabs(z) / zm < margin) margin = fabs(z) / zm;
+      } else {
+        an[j] = z; amn[j] = zm; z_out = z; zm_out = zm;
+      }
+    }
+    W += (int64_t)din * dout;
+    a = an; am = amn;
+  }
+  double y = or_sigmoid(z_out);
+  *ymag = y + y * (1.0 - y) * zm_out;
+  *kink = margin;
+  return y;
+}
+
+/* Magnitudes of the encoded features, fmag [n][L*F]. */
+void or_encode_mag(int L, int F, int log2T, const int *res, const double *tables, const float *xyz, int64_t n,
+                   double *fmag) {
+#pragma omp parallel
+  {
+    double *f = (double *)malloc(sizeof(double) * L * F);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+      or_encode_point_mag(L, F, log2T, res, tables, xyz + 3 * i, f, fmag + i * (int64_t)L * F);
+    free(f);
+  }
+}
+
+/* Network values y, their magnitudes ymag and kink margins (all [n]). */
+void or_forward_mag(int L, int F, int log2T, const int *res, const int *dims, int n_dims, const double *params,
+                    const float *xyz, int64_t n, double *y, double *ymag, double *kink) {
+  int64_t T = (int64_t)1 << log2T;
+  const double *weights = params + (int64_t)L * T * F;
+  int alen = or_act_len(dims, n_dims);
+#pragma omp parallel
+  {
+    double *act = (double *)malloc(sizeof(double) * alen);
+    double *actm = (double *)malloc(sizeof(double) * alen);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      or_encode_point_mag(L, F, log2T, res, params, xyz + 3 * i, act, actm);
+      y[i] = or_mlp_point_mag(dims, n_dims, weights, act, actm, &ymag[i], &kink[i]);
+    }
+    free(act); free(actm);
+  }
+}
+
+/* The chain of or_point_df with magnitudes for one point, upstream magnitude
+ * dym: M(sigma') = y (1 - y) + |1 - 2y| M(y); M(delta_out) = dym M(sigma');
+ * M(dW_k[j][c]) += M(delta_k[j]) M(a_k[c]) (into gwm when given);
+ * M(delta_{k-1}[c]) = 1[z > 0] Sum_j |W_k[j][c]| M(delta_k[j]) (masked == 0:
+ * without 1[z > 0]); M(df) = |W_0|^T M(delta_0), left in dm[0 .. L*F). */
+static void or_point_dfmag(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
+                           const double *params, const float *x, double dym, int masked, double *gwm,
+                           double *act, double *actm, double *dm, double *dinm) {
+  uint32_t T = 1u << log2T;
+  const double *weights = params + (int64_t)L * T * F;
+  int nl = n_dims - 1;
+  double ym, kink;
+  or_encode_point_mag(L, F, log2T, res, params, x, act, actm);
+  double y = or_mlp_point_mag(dims, n_dims, weights, act, actm, &ym, &kink);
+  double sp = y * (1.0 - y);
+  dm[0] = dym * (sp + fabs(1.0 - 2.0 * y) * ym);
+  for (int k = nl - 1; k >= 0; --k) {
+    int ind = dims[k], outd = dims[k + 1];
+    int64_t woff = 0, aoff = 0;
+    for (int q = 0; q < k; ++q) { woff += (int64_t)dims[q] * dims[q + 1]; aoff += dims[q]; }
+    const double *Wk = weights + woff;
+    const double *ak = act + aoff, *akm = actm + aoff;
+    if (gwm) {
+      double *gWk = gwm + woff;
+      for (int j = 0; j < outd; ++j)
+        for (int c = 0; c < ind; ++c) gWk[(int64_t)j * ind + c] += dm[j] * akm[c];
+    }
+    for (int c = 0; c < ind; ++c) {
+      double sm = 0.0;
+      for (int j = 0; j < outd; ++j) sm += fabs(Wk[(int64_t)j * ind + c]) * dm[j];
+      dinm[c] = (k > 0 && masked && !(ak[c] > 0.0)) ? 0.0 : sm;
+    }
+    memcpy(dm, dinm, sizeof(double) * ind);
+  }
+}
+
+/* Magnitudes of the parameter gradient of or_backward for upstream gradients
+ * of magnitude dy_mag [n] (|dL/dy| for a given upstream gradient), added into
+ * gmag [n_params] (tables, then weights): the weight magnitudes of
+ * or_point_dfmag, and M(dtheta) += w M(df) at every corner. */
+void or_backward_mag(int L, int F, int log2T, const int *res, const int *dims, int n_dims, const double *params,
+                     const float *xyz, int64_t n, const double *dy_mag, int masked, double *gmag) {
+  uint32_t T = 1u << log2T;
+  int64_t tab = (int64_t)L * T * F;
+  int alen = or_act_len(dims, n_dims);
+  int mx = or_max_dim(dims, n_dims);
+  double *act = (double *)malloc(sizeof(double) * alen);
+  double *actm = (double *)malloc(sizeof(double) * alen);
+  double *dm = (double *)malloc(sizeof(double) * mx);
+  double *dinm = (double *)malloc(sizeof(double) * mx);
+  for (int64_t i = 0; i < n; ++i) {
+    const float *x = xyz + 3 * i;
+    or_point_dfmag(L, F, log2T, res, dims, n_dims, params, x, dy_mag[i], masked, gmag + tab, act, actm, dm, dinm);
+    for (int l = 0; l < L; ++l) {
+      int64_t c[3]; double w[3];
+      for (int a = 0; a < 3; ++a) or_cell(x[a], res[l], &c[a], &w[a]);
+      for (int d = 0; d < 8; ++d) {
+        int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+        double wt = (dx ? w[0] : 1.0 - w[0]) * (dy ? w[1] : 1.0 - w[1]) * (dz ? w[2] : 1.0 - w[2]);
+        uint32_t h = or_hash(c[0] + dx, c[1] + dy, c[2] + dz, T);
+        double *g = gmag + ((int64_t)l * T + h) * F;
+        for (int j = 0; j < F; ++j) g[j] += wt * dm[l * F + j];
+      }
+    }
+  }
+  free(act); free(actm); free(dm); free(dinm);
+}
+
+/* Magnitudes of or_backward_x's coordinate gradient, dxyz_mag [n][3]: per
+ * level and corner, N_l |d(weight)/dx_a| times Sum_j |theta_j| M(df_j), with
+ * M(df) from or_point_dfmag (upstream magnitudes dy_mag). */
+void or_backward_x_mag(int L, int F, int log2T, const int *res, const int *dims, int n_dims,
+                       const double *params, const float *xyz, int64_t n, const double *dy_mag, int masked,
+                       double *dxyz_mag) {
+  uint32_t T = 1u << log2T;
+  int alen = or_act_len(dims, n_dims);
+  int mx = or_max_dim(dims, n_dims);
+#pragma omp parallel
+  {
+    double *act = (double *)malloc(sizeof(double) * alen);
+    double *actm = (double *)malloc(sizeof(double) * alen);
+    double *dm = (double *)malloc(sizeof(double) * mx);
+    double *dinm = (double *)malloc(sizeof(double) * mx);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      const float *x = xyz + 3 * i;
+      or_point_dfmag(L, F, log2T, res, dims, n_dims, params, x, dy_mag[i], masked, NULL, act, actm, dm, dinm);
+      double gx[3] = {0.0, 0.0, 0.0};
+      for (int l = 0; l < L; ++l) {
+        int64_t c[3]; double w[3];
+        for (int a = 0; a < 3; ++a) or_cell(x[a], res[l], &c[a], &w[a]);
+        for (int d = 0; d < 8; ++d) {
+          int dd[3] = {d & 1, (d >> 1) & 1, (d >> 2) & 1};
+          uint32_t h = or_hash(c[0] + dd[0], c[1] + dd[1], c[2] + dd[2], T);
+          const double *e = params + ((int64_t)l * T + h) * F;
+          double dot = 0.0;
+          for (int j = 0; j < F; ++j) dot += fabs(e[j]) * dm[l * F + j];
+          for (int a = 0; a < 3; ++a) {
+            double dw = 1.0;
+            for (int o = 0; o < 3; ++o)
+              if (o != a) dw *= dd[o] ? w[o] : 1.0 - w[o];
+            gx[a] += (double)res[l] * dw * dot;
+          }
+        }
+      }
+      for (int a = 0; a < 3; ++a) dxyz_mag[3 * i + a] = gx[a];
+    }
+    free(act); free(actm); free(dm); free(dinm);
+  }
+}
+
 /* A-8: textbook Adam (Kingma & Ba), as the paper's optimizer (Sec. 3.1, App. B),
  * dense over every parameter, bias-corrected, step t counted from 1.  l2 is the
  * weight-decay term added to the gradient before the moments. */
 void or_adam(double *p, const double *g, double *m, double *v, int64_t n, int t,
              double lr, double b1, double b2, double eps, double l2) {
   double bc1 = 1.0 - pow(b1, (double)t), bc2 = 1.0 - pow(b2, (double)t);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double gi = g[i] + l2 * p[i];
     m[i] = b1 * m[i] + (1.0 - b1) * gi;
@@ -709,6 +957,20 @@ static void or_tf(const float *lut, double v, double *rgba) {
   for (int c = 0; c < 4; ++c) rgba[c] = (1.0 - w) * (double)lut[4 * i + c] + w * (double)lut[4 * (i + 1) + c];
 }
 
+/* Magnitudes of or_tf's output for a value of magnitude vm: the two LUT terms
+ * plus the slope of the piece times vm (taken whether or not v was clamped:
+ * a value at the clamp may fall either side of it). */
+static void or_tf_mag(const float *lut, double v, double vm, double *rgbam) {
+  double u = (v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v)) * 255.0;
+  int i = (int)floor(u);
+  if (i > 254) i = 254;
+  double w = u - (double)i;
+  for (int c = 0; c < 4; ++c) {
+    double l0 = (double)lut[4 * i + c], l1 = (double)lut[4 * (i + 1) + c];
+    rgbam[c] = (1.0 - w) * fabs(l0) + w * fabs(l1) + 255.0 * fabs(l1 - l0) * vm;
+  }
+}
+
 /* What one sample sees: the network (use_net) or the raw volume by trilinear
  * interpolation. */
 typedef struct {
@@ -731,6 +993,30 @@ static double or_field_value(const or_field *f, const float *pos, double *act) {
   return or_trilinear_point(f->vol, f->nx, f->ny, f->nz, pos);
 }
 
+/* The same value with its magnitude *vm: the network's (or_mlp_point_mag) or,
+ * for the raw volume, the trilinear sum of |voxel| (actm: NULL for the raw
+ * volume). */
+static double or_field_value_mag(const or_field *f, const float *pos, double *act, double *actm, double *vm) {
+  if (f->use_net) {
+    double kink;
+    or_encode_point_mag(f->L, f->F, f->log2T, f->res, f->params, pos, act, actm);
+    return or_mlp_point_mag(f->dims, f->n_dims, f->weights, act, actm, vm, &kink);
+  }
+  int i0[3]; double w[3];
+  or_voxel_axis(pos[0], f->nx, &i0[0], &w[0]);
+  or_voxel_axis(pos[1], f->ny, &i0[1], &w[1]);
+  or_voxel_axis(pos[2], f->nz, &i0[2], &w[2]);
+  double m = 0.0;
+  for (int d = 0; d < 8; ++d) {
+    int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+    int ix = i0[0] + (f->nx > 1 ? dx : 0), iy = i0[1] + (f->ny > 1 ? dy : 0), iz = i0[2] + (f->nz > 1 ? dz : 0);
+    double wt = (dx ? w[0] : 1.0 - w[0]) * (dy ? w[1] : 1.0 - w[1]) * (dz ? w[2] : 1.0 - w[2]);
+    m += wt * fabs((double)f->vol[((int64_t)iz * f->ny + iy) * f->nx + ix]);
+  }
+  *vm = m;
+  return or_trilinear_point(f->vol, f->nx, f->ny, f->nz, pos);
+}
+
 /* The march of one ray from t0 to t1 (Sec. 5.2.1, 5.3).  Fixed step: samples
  * at t_k = t0 + (k + 1/2) step while t_k < t1, a sample whose macrocell has
  * mu_max == 0 skipped, opacity exponent alpha_exp.  Adaptive step
@@ -742,8 +1028,9 @@ static double or_field_value(const or_field *f, const float *pos, double *act) {
  * with T the product of (1 - a'), same stop. */
 static void or_march(const or_field *f, const float *lut, const or_opts *opt, const float *o, const float *d,
                      float t0, float t1, int transmit, double *act, double *C, double *A, float *best_pos,
-                     double *best_w) {
+                     double *best_w, double *actm, double *Cm, double *Am) {
   double Ca[3] = {0, 0, 0}, Aa = 0.0, bw = 0.0;
+  double Cma[3] = {0, 0, 0}, Ama = 0.0;
   float t = t0;
   for (int64_t k = 0;; ++k) {
     float pos[3];
@@ -768,10 +1055,22 @@ static void or_march(const or_field *f, const float *lut, const or_opts *opt, co
         if (f->mumax[((int64_t)cz * f->ncy + cy) * f->ncx + cx] == 0.0f) continue;
       }
     }
-    double c[4];
-    or_tf(lut, or_field_value(f, pos, act), c);
+    double c[4], cm[4], vm = 0.0;
+    double v = Am ? or_field_value_mag(f, pos, act, actm, &vm) : or_field_value(f, pos, act);
+    or_tf(lut, v, c);
     double a = 1.0 - pow(1.0 - c[3], e);
     double w = (1.0 - Aa) * a;
+    if (Am) {
+      /* magnitudes: a' = 1 - (1 - a)^e has slope e (1 - a)^(e - 1) (infinite at
+       * a = 1 for e < 1); w = (1 - A) a'; C and A sum the w terms */
+      or_tf_mag(lut, v, vm, cm);
+      double slope = (c[3] < 1.0) ? e * pow(1.0 - c[3], e - 1.0) : (e == 1.0 ? 1.0 : (e > 1.0 ? 0.0 : INFINITY));
+      double am = a + slope * cm[3];
+      double wm = ((1.0 - Aa) + Ama) * am;
+      if (!transmit)
+        for (int ch = 0; ch < 3; ++ch) Cma[ch] += wm * cm[ch];
+      Ama += wm;
+    }
     if (!transmit) {
       for (int ch = 0; ch < 3; ++ch) Ca[ch] += w * c[ch];
       if (w > bw) {
@@ -785,6 +1084,11 @@ static void or_march(const or_field *f, const float *lut, const or_opts *opt, co
   for (int ch = 0; ch < 3; ++ch) C[ch] = Ca[ch];
   *A = Aa;
   if (best_w) *best_w = bw;
+  if (Am) {
+    if (Cm)
+      for (int ch = 0; ch < 3; ++ch) Cm[ch] = Cma[ch];
+    *Am = Ama;
+  }
 }
 
 /* Sec. 5, 5.2.1, 5.3: the ray march of selected pixels, one ray at a time, every
@@ -801,7 +1105,7 @@ void or_render_pixels(const or_camera *cam, const float *lut, const or_opts *opt
                       int use_net, int L, int F, int log2T, const int *res, const int *dims, int n_dims,
                       const double *params,
                       const float *vol, int nx, int ny, int nz, const float *mumax,
-                      const int64_t *pix, int64_t npix, double *rgba_out) {
+                      const int64_t *pix, int64_t npix, double *rgba_out, double *mag_out) {
   or_field f;
   memset(&f, 0, sizeof(f));
   f.use_net = use_net; f.L = L; f.F = F; f.log2T = log2T; f.res = res; f.dims = dims; f.n_dims = n_dims;
@@ -818,32 +1122,41 @@ void or_render_pixels(const or_camera *cam, const float *lut, const or_opts *opt
 #pragma omp parallel
   {
     double *act = (double *)malloc(sizeof(double) * alen);
+    double *actm = (double *)malloc(sizeof(double) * alen);
 #pragma omp for schedule(dynamic, 16)
     for (int64_t q = 0; q < npix; ++q) {
       int64_t p = pix[q];
       int px = (int)(p % cam->width), py = (int)(p / cam->width);
       float o[3], d[3], t0, t1;
-      double C[3] = {0, 0, 0}, A = 0.0;
+      double C[3] = {0, 0, 0}, A = 0.0, Cm[3] = {0, 0, 0}, Am = 0.0;
+      double *am = mag_out ? &Am : NULL;
       or_ray(cam, px, py, o, d);
       if (or_box(o, d, &t0, &t1)) {
         float best[3] = {0, 0, 0};
         double bw = 0.0;
-        or_march(&f, lut, opt, o, d, t0, t1, 0, act, C, &A, best, &bw);
+        or_march(&f, lut, opt, o, d, t0, t1, 0, act, C, &A, best, &bw, actm, Cm, am);
         if (opt->shade == 1 && bw > 0.0) {
           float s0, s1;
-          double Cs[3], As = 0.0;
+          double Cs[3], As = 0.0, Asm = 0.0;
           if (or_box(best, opt->light, &s0, &s1))
-            or_march(&f, lut, opt, best, opt->light, s0, s1, 1, act, Cs, &As, NULL, NULL);
-          double k = (double)opt->ambient + (1.0 - (double)opt->ambient) * (1.0 - As);
-          for (int ch = 0; ch < 3; ++ch) C[ch] *= k;
+            or_march(&f, lut, opt, best, opt->light, s0, s1, 1, act, Cs, &As, NULL, NULL, actm, NULL,
+                     mag_out ? &Asm : NULL);
+          double amb = (double)opt->ambient;
+          double k = amb + (1.0 - amb) * (1.0 - As);
+          double km = amb + (1.0 - amb) * ((1.0 - As) + Asm);
+          for (int ch = 0; ch < 3; ++ch) { C[ch] *= k; Cm[ch] *= km; }
         }
       }
       rgba_out[4 * q + 0] = C[0];
       rgba_out[4 * q + 1] = C[1];
       rgba_out[4 * q + 2] = C[2];
       rgba_out[4 * q + 3] = A;
+      if (mag_out) {
+        for (int ch = 0; ch < 3; ++ch) mag_out[4 * q + ch] = Cm[ch];
+        mag_out[4 * q + 3] = Am;
+      }
     }
-    free(act);
+    free(act); free(actm);
   }
 }
 

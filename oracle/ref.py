@@ -80,6 +80,13 @@ def lib():
                                   C.c_int64, _f64p, _f64p]
         L.or_backward_x.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
                                     C.c_int64, _f64p, _f64p]
+        L.or_encode_mag.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _f64p, _f32p, C.c_int64, _f64p]
+        L.or_forward_mag.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
+                                     C.c_int64, _f64p, _f64p, _f64p]
+        L.or_backward_mag.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
+                                      C.c_int64, _f64p, C.c_int, _f64p]
+        L.or_backward_x_mag.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f32p,
+                                        C.c_int64, _f64p, C.c_int, _f64p]
         L.or_adam.argtypes = [_f64p, _f64p, _f64p, _f64p, C.c_int64, C.c_int, C.c_double,
                               C.c_double, C.c_double, C.c_double, C.c_double]
         L.or_train_step.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, C.c_int, _f64p, _f64p,
@@ -100,7 +107,7 @@ def lib():
         L.or_render_pixels.argtypes = [C.POINTER(_Cam), _f32p, C.POINTER(_Opts), C.c_int, C.c_int,
                                        C.c_int, C.c_int, _i32p, _i32p, C.c_int, C.c_void_p,
                                        C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, _i64p,
-                                       C.c_int64, _f64p]
+                                       C.c_int64, _f64p, C.c_void_p]
         L.or_pixel_ray.argtypes = [C.POINTER(_Cam), C.c_int, C.c_int, _f32p, _f32p, _f32p]
         L.or_pixel_ray.restype = C.c_int
         L.or_box_exit.argtypes = [_f32p, _f32p]
@@ -250,6 +257,45 @@ def backward_x(net: Net, params, xyz, dL_dy):
     out = np.zeros((xyz.shape[0], 3), dtype=np.float64)
     lib().or_backward_x(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims), _f64(params),
                         xyz, xyz.shape[0], _f64(dL_dy), out)
+    return out
+
+
+def encode_mag(net: Net, params, xyz):
+    """Error magnitudes of the encoded features, [n][L*F] (Sum over corners of w |theta|)."""
+    xyz = _f32(xyz)
+    n = xyz.shape[0]
+    out = np.zeros((n, net.L * net.F), dtype=np.float64)
+    lib().or_encode_mag(net.L, net.F, net.log2T, net.res, _f64(params), xyz, n, out)
+    return out
+
+
+def forward_mag(net: Net, params, xyz):
+    """(y, M(y), kink margin) of every point: the network value, its error
+    magnitude and the smallest |z| / M(z) over the hidden units."""
+    xyz = _f32(xyz)
+    n = xyz.shape[0]
+    y, ym, kink = (np.zeros(n, dtype=np.float64) for _ in range(3))
+    lib().or_forward_mag(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims), _f64(params),
+                         xyz, n, y, ym, kink)
+    return y, ym, kink
+
+
+def backward_mag(net: Net, params, xyz, dy_mag, masked=True):
+    """Error magnitudes of the parameter gradient (laid out like params) for
+    upstream gradients of magnitude dy_mag; masked=False counts every ReLU unit."""
+    xyz = _f32(xyz)
+    g = np.zeros(net.n_params, dtype=np.float64)
+    lib().or_backward_mag(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims), _f64(params),
+                          xyz, xyz.shape[0], _f64(dy_mag), int(bool(masked)), g)
+    return g
+
+
+def backward_x_mag(net: Net, params, xyz, dy_mag, masked=True):
+    """Error magnitudes of the coordinate gradient, [n][3]."""
+    xyz = _f32(xyz)
+    out = np.zeros((xyz.shape[0], 3), dtype=np.float64)
+    lib().or_backward_x_mag(net.L, net.F, net.log2T, net.res, net._dims(), len(net.dims), _f64(params),
+                            xyz, xyz.shape[0], _f64(dy_mag), int(bool(masked)), out)
     return out
 
 
@@ -440,10 +486,11 @@ def box_exit(o, d):
 
 
 def render_pixels(cam: dict, lut, opts: dict, pixels, net: Net | None = None, params=None,
-                  vol=None, mumax=None):
+                  vol=None, mumax=None, with_mag=False):
     """RGBA (FP64) of the listed pixels; network values if net is given, else the raw volume.
 
-    vol (with its dims) is also needed for macrocell skipping when mc_cell > 0."""
+    vol (with its dims) is also needed for macrocell skipping when mc_cell > 0.
+    with_mag: also return the error magnitudes of the four channels."""
     o = _Opts()
     o.step = float(opts["step"])
     o.alpha_exp = float(opts.get("alpha_exp", 1.0))
@@ -457,6 +504,8 @@ def render_pixels(cam: dict, lut, opts: dict, pixels, net: Net | None = None, pa
         raise ValueError("the adaptive step needs macrocells (mc_cell > 0)")
     pix = np.ascontiguousarray(pixels, dtype=np.int64)
     out = np.zeros((pix.shape[0], 4), dtype=np.float64)
+    mag = np.zeros((pix.shape[0], 4), dtype=np.float64) if with_mag else None
+    magp = mag.ctypes.data if with_mag else None
     if vol is not None:
         vol = _f32(vol)
         nz, ny, nx = vol.shape
@@ -472,12 +521,12 @@ def render_pixels(cam: dict, lut, opts: dict, pixels, net: Net | None = None, pa
         prm = _f64(params)
         lib().or_render_pixels(C.byref(_cam(cam)), _f32(lut), C.byref(o), 1, net.L, net.F, net.log2T,
                                net.res, net._dims(), len(net.dims), prm.ctypes.data, volp, nx, ny,
-                               nz, mup, pix, pix.shape[0], out)
+                               nz, mup, pix, pix.shape[0], out, magp)
     else:
         z = np.zeros(1, np.int32)
         lib().or_render_pixels(C.byref(_cam(cam)), _f32(lut), C.byref(o), 0, 0, 0, 0, z, z, 0, None,
-                               volp, nx, ny, nz, mup, pix, pix.shape[0], out)
-    return out
+                               volp, nx, ny, nz, mup, pix, pix.shape[0], out, magp)
+    return (out, mag) if with_mag else out
 
 
 def mse(a, b):

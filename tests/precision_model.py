@@ -49,6 +49,50 @@ def backward_model(net: O.Net, params, xyz, dy, prec, scale=128.0):
     return dF, (dZ1.T @ f) / scale, (dZ2.T @ h1) / scale, (dz3 @ h2) / scale
 
 
+def forward_model(net: O.Net, params, xyz, prec):
+    """Network outputs y with the kernel's rounding points for `prec`."""
+    rnd = ROUND[prec]
+    p = np.asarray(params, np.float64).copy()
+    p[: net.n_table] = rnd(p[: net.n_table])
+    d = net.dims
+    W = p[net.n_table:]
+    W0 = W[: d[1] * d[0]].reshape(d[1], d[0])
+    W1 = W[d[1] * d[0]: d[1] * d[0] + d[2] * d[1]].reshape(d[2], d[1])
+    W2 = W[-d[2]:]
+    f = rnd(O.encode(net, p, xyz))
+    h1 = rnd(np.maximum(f @ rnd(W0).T, 0))
+    h2 = np.maximum(h1 @ rnd(W1).T, 0)
+    return 1 / (1 + np.exp(-(h2 @ W2)))
+
+
+def table_grad_from_df(net: O.Net, xyz, dF):
+    """The table gradient [n_table] of per-point input gradients dF [n][L*F]:
+    every cell corner of every level adds its trilinear weight times dF (FP64;
+    corner order and cells from the oracle's hash indices and FP32 scaling)."""
+    xyz = np.asarray(xyz, np.float32)
+    idx = O.hash_indices(net, xyz).astype(np.int64)  # [n][L][8], corner d = dx + 2 dy + 4 dz
+    F, T = net.F, net.T
+    g = np.zeros(net.n_table)
+    for l, N in enumerate(net.res):
+        pc = xyz * np.float32(N)  # the kernel's single FP32 multiply
+        w = pc.astype(np.float64) - np.floor(pc.astype(np.float64))
+        df = dF[:, l * F:(l + 1) * F]
+        for d in range(8):
+            wt = np.ones(xyz.shape[0])
+            for a in range(3):
+                wt *= w[:, a] if (d >> a) & 1 else 1.0 - w[:, a]
+            slot = (l * T + idx[:, l, d])[:, None] * F + np.arange(F)[None, :]
+            np.add.at(g, slot.ravel(), (wt[:, None] * df).ravel())
+    return g
+
+
+def grads_model(net: O.Net, params, xyz, dy, prec, scale=128.0):
+    """The whole parameter gradient (tables then W0, W1, W2) with the kernel's
+    rounding points for `prec`."""
+    dF, dW0, dW1, dW2 = backward_model(net, params, xyz, dy, prec, scale)
+    return np.concatenate([table_grad_from_df(net, xyz, dF), dW0.ravel(), dW1.ravel(), np.ravel(dW2)])
+
+
 def normwise(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 

@@ -45,9 +45,9 @@ def test_adaptive_raw_volume_matches_oracle(nv, cell, smax, K):
     cam = I.perspective_camera(80, 60)
     r = nv.Renderer(80 * 60, K=K)
     img = r.render(cam, lt, opts, raw=vt, mc=(mu, cell, vol.shape)).cpu().numpy()
-    want = O.render_pixels(cam, lut, opts, np.arange(80 * 60), vol=vol, mumax=mu.cpu().numpy())
+    want = O.render_pixels(cam, lut, opts, np.arange(80 * 60), vol=vol, mumax=mu.cpu().numpy(), with_mag=True)
     _compare_images(img, want)
-    assert want[:, 3].max() > 0.5
+    assert want[0][:, 3].max() > 0.5
 
 
 def test_adaptive_network_fp32_matches_oracle(nv):
@@ -64,7 +64,8 @@ def test_adaptive_network_fp32_matches_oracle(nv):
     cam = I.perspective_camera(48, 40)
     img = nv.Renderer(48 * 40, K=8).render(cam, lt, opts, net=net, mc=(mu, 8, vol.shape)).cpu().numpy()
     pix = np.random.default_rng(2).choice(48 * 40, 400, replace=False)
-    want = O.render_pixels(cam, lut, opts, pix, net=onet(c), params=params, vol=vol, mumax=mu.cpu().numpy())
+    want = O.render_pixels(cam, lut, opts, pix, net=onet(c), params=params, vol=vol, mumax=mu.cpu().numpy(),
+                           with_mag=True)
     _compare_images(img.reshape(-1, 4)[pix], want)
 
 

@@ -90,5 +90,6 @@ def test_cfg5_ring_of_64_cubed_bricks_matches_oracle(nv):
         ox, ot = O.brick_sample(vol, 64, np.array(slots, np.int32), 11, step, n)
         np.testing.assert_array_equal(xyz.cpu().numpy(), ox)
         got = t.cpu().numpy().astype(np.float64)
-        assert np.max(np.abs(got - ot) / np.maximum(np.abs(ot), 1e-2 * np.abs(ot).max())) <= 1e-5
+        # trilinear of voxels >= 0: the error magnitude is the value itself
+        assert np.all(np.abs(got - ot) <= 1e-5 * np.abs(ot))
     ring.close()

@@ -103,12 +103,13 @@ def test_fp16_overflow_skips_the_step_and_halves_the_scale(nv):
     g1 = tr.grads.copy()
     tr.step(x2, t2)
     g2 = tr.grads
-    clear = (np.abs(g1) > 0.05 * np.abs(g1).max()) & (np.abs(g2) > 0.05 * np.abs(g2).max())
-    assert clear.sum() > 100
+    clear = (np.abs(g1) > 1e-2 * np.abs(g1).max()) & (np.abs(g2) > 1e-2 * np.abs(g2).max())
+    assert clear.sum() > 500
     assert np.max(np.abs(got[clear] - ref[clear])) <= 1e-6
-    # and to the oracle's second Adam step (bias corrections of t = 2): the
-    # 16-bit gradients move a second-step update by about a percent of lr,
-    # while counting the skipped step (t = 3) would move it by ~14%
+    # and to the oracle's second Adam step (bias corrections of t = 2): 5% noise
+    # on both gradients moves a second-step update by < 2% of lr at the 99th
+    # percentile, while counting the skipped step (t = 3) moves every one of
+    # these by > 5% of lr (median 11%)
     dp_got = got - params
     dp_want = tr.params - params
     agree = np.abs(dp_got[clear] - dp_want[clear]) <= 0.05 * LR

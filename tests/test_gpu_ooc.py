@@ -40,7 +40,8 @@ def test_ring_samples_match_oracle(nv):
         ox, ot = O.brick_sample(vol, 16, np.array(slots, np.int32), 9, step, n)
         np.testing.assert_array_equal(xyz.cpu().numpy(), ox)
         got = t.cpu().numpy().astype(np.float64)
-        assert np.max(np.abs(got - ot) / np.maximum(np.abs(ot), 1e-2 * np.abs(ot).max())) <= 1e-5
+        # trilinear of voxels >= 0: the error magnitude is the value itself
+        assert np.all(np.abs(got - ot) <= 1e-5 * np.abs(ot))
     b, ms = ring.stats()
     assert b == (3 + 6) * 18 ** 3 * 4
     ring.close()

@@ -3,7 +3,8 @@ against the oracle: the primary march, the choice of the sample of largest
 contribution and the shadow march from it follow the same FP32 positions; the
 values follow the FP32 tolerance.  A pixel whose largest contribution is a
 near tie may pick the other sample on one side, which moves its shadow: such
-pixels are counted and must be rare."""
+pixels are counted and must be rare.  The per-channel bound is 1e-5 of the
+oracle's error magnitude of the channel (as in tests/test_gpu_parity.py)."""
 import numpy as np
 import pytest
 import torch
@@ -27,13 +28,14 @@ def nv():
 
 
 def _compare(got, want, max_frac=0.01):
+    """Per channel |g - o| <= TOL M, M the oracle's error magnitude of the channel."""
+    want, mag = want
     got = got.reshape(-1, 4).astype(np.float64)
-    den = np.maximum(np.abs(want), 1e-2 * max(np.abs(want).max(), 1e-30))
-    bad = (np.abs(got - want) / den > TOL).any(axis=1)
+    bad = (np.abs(got - want) > TOL * mag).any(axis=1)
     assert bad.mean() <= max_frac, (bad.sum(), len(bad))
     # the opacity channel is the emission-absorption one: unaffected by the shadow choice
     term = np.maximum(got[:, 3], want[:, 3]) >= 0.99 - 1e-4
-    a_bad = (np.abs(got[:, 3] - want[:, 3]) / den[:, 3] > TOL) & ~term
+    a_bad = (np.abs(got[:, 3] - want[:, 3]) > TOL * mag[:, 3]) & ~term
     assert not a_bad.any()
     return int(bad.sum())
 
@@ -53,7 +55,7 @@ def test_shadow_raw_volume_matches_oracle(nv, light, adaptive):
     cam = I.perspective_camera(72, 54)
     r = nv.Renderer(72 * 54, K=8)
     img = r.render(cam, lt, opts, raw=vt, mc=(mu, 8, vol.shape)).cpu().numpy()
-    want = O.render_pixels(cam, lut, opts, np.arange(72 * 54), vol=vol, mumax=mu.cpu().numpy())
+    want = O.render_pixels(cam, lut, opts, np.arange(72 * 54), vol=vol, mumax=mu.cpu().numpy(), with_mag=True)
     _compare(img, want)
     ea = r.render(cam, lt, dict(opts, shade=0), raw=vt, mc=(mu, 8, vol.shape)).cpu().numpy().reshape(-1, 4)
     assert np.all(img.reshape(-1, 4)[:, :3] <= ea[:, :3] + 1e-6)
@@ -99,7 +101,8 @@ def test_shadow_network_fp32_matches_oracle(nv):
     cam = I.perspective_camera(40, 32)
     img = nv.Renderer(40 * 32, K=8).render(cam, lt, opts, net=net, mc=(mu, 8, vol.shape)).cpu().numpy()
     pix = np.random.default_rng(2).choice(40 * 32, 300, replace=False)
-    want = O.render_pixels(cam, lut, opts, pix, net=onet(c), params=params, vol=vol, mumax=mu.cpu().numpy())
+    want = O.render_pixels(cam, lut, opts, pix, net=onet(c), params=params, vol=vol, mumax=mu.cpu().numpy(),
+                           with_mag=True)
     _compare(img.reshape(-1, 4)[pix], want, max_frac=0.02)
 
 
