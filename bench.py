@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "fp16", "bf16"])
-    ap.add_argument("--cpu-points", type=int, default=32768, help="oracle sample size (points)")
+    ap.add_argument("--cpu-points", type=int, default=1 << 18, help="oracle sample size (points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default="", choices=["", "render1080p"],
                     help="run one profiling case instead of the benchmark")
@@ -145,9 +145,9 @@ def oracle_step_rate(cpu_points: int):
     per_point = max(t_step - t_adam, 1e-12) / cpu_points
     batch = CF.CFG2["batch"]
     rate = batch / (t_adam + batch * per_point)
-    desc = (f"one oracle training step on {cpu_points} of the 2^18 config-2 points (forward on "
-            f"{O.num_threads()} threads, backward serial) + one dense Adam over {net.n_params} params; "
-            f"per-point cost extrapolated to a 2^18-point step")
+    desc = (f"one oracle training step on {cpu_points} of the 2^18 config-2 points (forward, backward and "
+            f"the dense Adam over {net.n_params} params on {O.num_threads()} threads); per-point cost "
+            f"extrapolated to a 2^18-point step")
     return rate, O.num_threads(), t_step + t_adam, desc
 
 
@@ -161,7 +161,7 @@ def run_reference(args):
     desc = ""
     threads = 1
     for i in range(args.warmup + args.steps):
-        r, threads, s, desc = oracle_step_rate(max(1024, args.cpu_points // 4))
+        r, threads, s, desc = oracle_step_rate(args.cpu_points)  # the sample of ours' cpu_baseline
         if i >= args.warmup:
             rates.append(r)
             secs += s
@@ -181,16 +181,40 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ roofline ---
 
+def csrc_digest():
+    """SHA-256 over the library's CUDA sources (file names and contents, sorted)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2207_11620_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
 def ncu_traffic(kernel):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, or None."""
+    """(DRAM bytes per launch of a kernel from the committed ncu summary, note).
+
+    The summary records the digest of the CUDA sources it was captured from; once
+    the sources differ the figure no longer describes the kernel and is withheld."""
     p = os.path.join(ROOT, "profiles", "dram_traffic_cfg2.txt")
     if not os.path.exists(p):
-        return None
+        return None, "no committed capture"
+    digest, val = None, None
     for line in open(p):
+        if line.startswith("# csrc_sha256"):
+            digest = line.split()[-1]
         f = line.split("#", 1)[0].split()
         if len(f) >= 2 and f[0] == kernel:
-            return int(f[1])
-    return None
+            val = int(f[1])
+    if val is None:
+        return None, "kernel not in the committed capture"
+    if digest != csrc_digest():
+        return None, "kernel sources changed since the committed capture (profiles/dram_traffic_cfg2.txt)"
+    return val, "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, committed capture " \
+                "(profiles/dram_traffic_cfg2.txt) of these sources"
 
 
 def l2_peaks(nv, torch):
@@ -216,10 +240,12 @@ def l2_peaks(nv, torch):
         return ops / (statistics.median(ts) / 1e3)
     red = rate(lambda s: nv.peak_scatter(red_buf, ops, seed=s))
     ld = rate(lambda s: nv.peak_gather(ld_buf, ops, sink, seed=s))
+    l1 = rate(lambda s: nv.peak_gather(ld_buf[: 1 << 11], ops, sink, seed=s))
     del red_buf, ld_buf
-    return {"scatter_reductions_per_s": red, "gather_loads_per_s": ld,
-            "how": "2^26 scattered 16-byte FP32 vector reductions into 64 MiB / 16-byte loads from 32 MiB, "
-                   "median of 5 launches (nv_peak_scatter / nv_peak_gather)"}
+    return {"scatter_reductions_per_s": red, "gather_loads_per_s": ld, "l1_gather_loads_per_s": l1,
+            "how": "2^26 scattered 16-byte FP32 vector reductions into 64 MiB / 16-byte loads from 32 MiB / "
+                   "16-byte loads from an L1-resident 32 KiB, median of 5 launches (nv_peak_scatter / "
+                   "nv_peak_gather)"}
 
 
 def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_visit, n_table, d, L, F, l2pk=None):
@@ -228,70 +254,73 @@ def roofline_of(kind, avg, prec, pk, pk_kind, batch, n_visit, n_table, d, L, F, 
     Algorithmic bytes / FLOPs per launch (per unit x units):
       adam     34 B per parameter it visits (read p, g, m, v; write p, m, v, g = 0, 16-bit shadow);
                32 in FP32.  n_visit: the parameters in blocks that hold a weight or a hash slot a
-               point of [0,1]^3 can reach (nv_adam_span); the other blocks stay unchanged
-      encode   per point: 8 corners x L levels x F 16-bit features read (8 L F 2 B) + the 16-bit
-               feature row written (2 D0 B) + the trilinear target (8 voxels read, 4 B written)
-      mlp      tensor-core path, per point: the feature row read (2 D0 B) + the target (4 B) + the
-               table-gradient scatter, 8 corners x L x F FP32 reductions (8 L F 4 B); also reported:
-               tensor FLOPs 2 (D0 64 + 64 64) forward + 2 (2 64 64 + 2 64 D0) backward.
-               FP32 path: those FLOPs on CUDA cores"""
+               point of [0,1]^3 can reach (nv_adam_span); the other blocks stay unchanged.  Bound: HBM
+      encode   per point: 8 corners x L levels x F 16-bit features gathered (8 L F 2 B) + the 8
+               voxels of the trilinear target (32 B).  Bound: scattered loads that resolve in L1 / L2
+               (the 16-bit tables are L2-resident), against the measured rate of scattered 16-byte
+               loads x 16 B.  Also reported against HBM: those bytes + the feature row (2 D0 B) and
+               target (4 B) written
+      mlp      tensor-core path, per point: the table-gradient scatter, 8 corners x L x F FP32
+               reductions (8 L F 4 B).  Bound: scattered vector reductions that resolve in L2 (the
+               FP32 table gradient is L2-resident), against the measured rate of scattered 16-byte
+               FP32 reductions x 16 B.  Also reported: against HBM, those bytes + the feature row
+               read (2 D0 B) + the target (4 B); tensor FLOPs 2 (D0 64 + 64 64) forward + 2 (2 64 64
+               + 2 64 D0) backward.  FP32 path: those FLOPs on CUDA cores"""
     ms = avg[kind]
     D0 = d[0]
     flops = 2 * batch * (D0 * 64 + 64 * 64) + 2 * batch * (2 * 64 * 64 + 2 * 64 * D0)
+    if kind == "mlp" and prec == "fp32":
+        ach = flops / (ms / 1e3) / 1e12
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return {"kernel": "k_mlp_f32", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "traffic_note": "not captured",
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x max SM clock",
+                "algorithmic_flops_per_launch": flops, "avg_ms": ms}
+    name = {"adam": "k_adam", "encode": "k_encode_tiles", "mlp": "k_mlp_tc"}[kind]
+    traffic, note = ncu_traffic(name)
     if kind == "adam":
         bytes_ = n_visit * (32 + (2 if prec != "fp32" else 0))
-        name = "k_adam"
-    elif kind == "encode":
-        bytes_ = batch * (8 * L * F * 2 + 2 * D0 + 8 * 4 + 4)
-        name = "k_encode_tiles"
-    elif prec != "fp32":
-        bytes_ = batch * (2 * D0 + 4 + 8 * L * F * 4)
-        name = "k_mlp_tc"
-    else:
-        bytes_ = None
-        name = "k_mlp_f32"
-    if bytes_ is not None:
         ach = bytes_ / (ms / 1e3) / 1e9
-        r = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-             "frac": ach / pk["hbm_gbs"], "traffic": ncu_traffic(name), "peak_kind": pk_kind + " (copy)",
-             "algorithmic_bytes_per_launch": bytes_, "avg_ms": ms}
-        if kind == "adam":
-            r["params_visited_per_launch"] = n_visit
-        if kind == "encode":
-            r["limiter"] = ("L1-to-L2 request rate of the scattered 32-byte sector gathers; coarse levels hit "
-                            "in L1 and the 16-bit tables in L2, so DRAM carries a fraction of these bytes")
-            if l2pk:  # 16-byte group loads: 5 per point and level at F = 2, 6 at F = 4, + 8 target voxels
-                loads = batch * (L * (5 if F == 2 else 6) + 8)
-                a = loads / (ms / 1e3)
-                r["gather_rate"] = {"loads_per_launch": loads, "achieved_per_s": a,
-                                    "peak_per_s": l2pk["gather_loads_per_s"], "frac": a / l2pk["gather_loads_per_s"],
-                                    "peak_kind": "measured (scattered 16-byte loads, 32 MiB)"}
-        elif kind == "mlp":
-            peak_t = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-            ach_t = flops / (ms / 1e3) / 1e12
-            r["limiter"] = ("L2 vector reductions of the fused table-gradient scatter, which resolve in L2 "
-                            "(the 64 MiB FP32 table gradient stays resident); the tensor pipe is not the limit")
-            r["tensor"] = {"achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s", "frac": ach_t / peak_t,
-                           "algorithmic_flops_per_launch": flops}
-            if l2pk:  # 6 vector reductions per point and level at F = 2 (x-paired), 8 at F = 4
-                reds = batch * L * (6 if F == 2 else 8)
-                a = reds / (ms / 1e3)
-                r["scatter_rate"] = {"reductions_per_launch": reds, "achieved_per_s": a,
-                                     "peak_per_s": l2pk["scatter_reductions_per_s"],
-                                     "frac": a / l2pk["scatter_reductions_per_s"],
-                                     "peak_kind": "measured (scattered 16-byte FP32 reductions, 64 MiB)"}
-        return r
-    ach = flops / (ms / 1e3) / 1e12
-    if prec == "fp32":
-        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
-                "algorithmic_flops_per_launch": flops, "avg_ms": ms}
-    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-    return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": ncu_traffic(name), "peak_kind": pk_kind + " (bf16 sustained)",
-            "algorithmic_flops_per_launch": flops, "avg_ms": ms}
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": traffic, "traffic_note": note,
+                "peak_kind": pk_kind + " (copy)", "algorithmic_bytes_per_launch": bytes_, "avg_ms": ms,
+                "params_visited_per_launch": n_visit}
+    if kind == "encode":
+        l2_bytes = batch * (8 * L * F * 2 + 8 * 4)
+        hbm_bytes = l2_bytes + batch * (2 * D0 + 4)
+        loads = batch * (L * (5 if F == 2 else 6) + 8)  # 16-byte loads issued: 5 per level at F = 2, 6 at F = 4
+        peak_rate = l2pk["gather_loads_per_s"]
+        kind_note = "measured: scattered 16-byte loads from 32 MiB (nv_peak_gather) x 16 B"
+        issued = {"loads_per_launch": loads, "achieved_per_s": loads / (ms / 1e3), "peak_per_s": peak_rate,
+                  "frac": loads / (ms / 1e3) / peak_rate}
+        limiter = ("L1 / L2 request rate of the scattered 16-byte gathers; the coarse levels hit in L1 and "
+                   "the 16-bit tables in L2, so DRAM carries a fraction of these bytes")
+    else:
+        l2_bytes = batch * (8 * L * F * 4)
+        hbm_bytes = l2_bytes + batch * (2 * D0 + 4)
+        reds = batch * L * (6 if F == 2 else 8)  # 16-byte reductions issued: 6 per level at F = 2 (x-paired)
+        peak_rate = l2pk["scatter_reductions_per_s"]
+        kind_note = "measured: scattered 16-byte FP32 vector reductions into 64 MiB (nv_peak_scatter) x 16 B"
+        issued = {"reductions_per_launch": reds, "achieved_per_s": reds / (ms / 1e3), "peak_per_s": peak_rate,
+                  "frac": reds / (ms / 1e3) / peak_rate}
+        limiter = ("L2 vector reductions of the fused table-gradient scatter (the FP32 table gradient stays "
+                   "L2-resident); the tensor pipe is not the limit")
+    ach = l2_bytes / (ms / 1e3) / 1e9
+    peak = peak_rate * 16 / 1e9
+    r = {"kernel": name, "bound": "l2", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+         "traffic": traffic, "traffic_note": note, "peak_kind": kind_note,
+         "algorithmic_bytes_per_launch": l2_bytes, "avg_ms": ms, "limiter": limiter,
+         "issued_16B_accesses": issued,
+         "hbm": {"achieved": hbm_bytes / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "frac": hbm_bytes / (ms / 1e3) / 1e9 / pk["hbm_gbs"], "peak_kind": pk_kind + " (copy)",
+                 "algorithmic_bytes_per_launch": hbm_bytes}}
+    if kind == "mlp":
+        peak_t = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        ach_t = flops / (ms / 1e3) / 1e12
+        r["tensor"] = {"achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s", "frac": ach_t / peak_t,
+                       "algorithmic_flops_per_launch": flops, "peak_kind": pk_kind + " (bf16 sustained; "
+                       "the FP16 dense rate is the same)"}
+    return r
 
 
 # ---------------------------------------------------------------------- ours ---
@@ -327,8 +356,30 @@ def run_ours(args):
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # one GPU: nv_train_step samples the batch inside its gather kernel.  N GPUs: data
+    # parallel (one network replicated, each rank sampling and training on its own
+    # 2^18-point shard of an N x 2^18 global batch, one all-reduce of the gradient per step)
+    if ws > 1:
+        from paper_2207_11620_gb300 import dp
+        dps = dp.DataParallelStep(net)
+
+        def step(i):
+            x, t = nv.sample(vol, batch, seed=1000 + rank, step=i)
+            return dps.step_shard(x, t, ws * batch)
+
+        def step_host(hx, ht):
+            return dps.step_shard(hx.cuda(non_blocking=True), ht.cuda(non_blocking=True), ws * batch)
+    else:
+        def step(i):
+            net.train_step(n=batch, vol=vol, seed=1000 + rank, loss_out=loss)
+            return loss
+
+        def step_host(hx, ht):
+            net.train_step(hx, ht, loss_out=loss)
+            return loss
+
     for i in range(args.warmup):
-        net.train_step(n=batch, vol=vol, seed=1000 + rank, loss_out=loss)
+        step(i)
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
@@ -338,7 +389,7 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for i in range(args.steps):
-        net.train_step(n=batch, vol=vol, seed=1000 + rank, loss_out=loss)
+        step(args.warmup + i)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -352,7 +403,7 @@ def run_ours(args):
     pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pe0.record(stream)
     for i in range(args.steps):
-        net.train_step(n=batch, vol=vol, seed=1000 + rank, loss_out=loss)
+        step(args.warmup + args.steps + i)
     pe1.record(stream)
     torch.cuda.synchronize()
     ms_profiled = pe0.elapsed_time(pe1)
@@ -373,15 +424,15 @@ def run_ours(args):
         host_t.append(t.cpu().pin_memory())
     loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
     for j in range(2):
-        net.train_step(host_x[j], host_t[j], loss_out=loss)
+        step_host(host_x[j], host_t[j])
     torch.cuda.synchronize()
     barrier(ws)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_wall = time.perf_counter()
     e0.record(stream)
     for i in range(args.steps):
-        net.train_step(host_x[i % n_e2e], host_t[i % n_e2e], loss_out=loss)
-        loss_host.copy_(loss, non_blocking=True)
+        lo = step_host(host_x[i % n_e2e], host_t[i % n_e2e])
+        loss_host.copy_(lo, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
@@ -418,18 +469,23 @@ def run_ours(args):
                    "adam_params_visited": n_visit,
                    "l2": "working set > L2: each step's Adam streams params, grads, m, v of the visited "
                          "blocks (%.0f MB)" % (n_visit * 16 / 1e6),
-                   "parallelism": "replicas" if ws > 1 else "single"},
+                   "parallelism": f"dp{ws}: one network, an all-reduce of its gradient per step" if ws > 1
+                                  else "single"},
         "roofline": roof,
         "rooflines_other_kernels": roof_others,
         "l2_access_peaks": l2pk,
         "kernels_ms_per_step": {k: v for k, v in avg.items() if v > 0},
         "ms_per_step_with_kernel_events": ms_profiled / args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": batch * 16, "d2h_bytes_per_step": 8},
-        "gpu_launches": args.steps * sum(1 for k in ("encode", "mlp", "scatter", "adam", "finish") if kt[k][1]),
+        "gpu_launches": args.steps * (sum(1 for k in ("encode", "mlp", "scatter", "adam", "finish") if kt[k][1])
+                                      + (1 if ws > 1 else 0)),
         "clocks": clk,
     }
+    if ws == 1:
+        line["render_1080p"] = bench_render_1080p(nv, I, CF, torch, min(max(args.steps, 3), 20), pk, pk_kind, l2pk,
+                                                  cpu=not args.no_cpu_baseline)
     if ws == 1 and args.extras:
-        line["extra"] = run_extras(args)
+        line["extra"] = run_extras(args, pk, pk_kind, l2pk)
     if ws == 1 and not args.no_cpu_baseline:
         rate, threads, secs, desc = oracle_step_rate(args.cpu_points)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
@@ -592,7 +648,129 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
     return out
 
 
-def extra_cfg4_inloop(nv, I, CF, torch, frames=None):
+def gather_roofline(ns, g_ms, L, F, D0, pk, pk_kind, l2pk):
+    """Roofline of the render gather (k_encode_tiles in inference) over one frame of ns
+    decoded samples: 8 corners x L levels x F 16-bit features per sample (512 B at L16
+    F2), 5 (F = 2) or 6 (F = 4) 16-byte loads issued per level.  The K samples of a
+    ray sit in adjacent lanes and share most corners, so these loads resolve in L1:
+    the bound is the measured rate of scattered 16-byte loads from an L1-resident
+    buffer (x 16 B); the same bytes are also set against the L2-resident scattered
+    load rate and, with the coordinates read (12 B) and the feature row written
+    (2 D0 B), against HBM."""
+    g_bytes = ns * 8 * L * F * 2
+    g_ach = g_bytes / (g_ms / 1e3) / 1e9
+    loads = ns * L * (5 if F == 2 else 6)
+    l1 = l2pk["l1_gather_loads_per_s"]
+    hbm = ns * (8 * L * F * 2 + 12 + 2 * D0) / (g_ms / 1e3) / 1e9
+    return {"kernel": "k_encode_tiles", "bound": "l1", "achieved": g_ach, "peak": l1 * 16 / 1e9, "unit": "GB/s",
+            "frac": g_ach / (l1 * 16 / 1e9),
+            "peak_kind": "measured: scattered 16-byte loads from an L1-resident 32 KiB (nv_peak_gather) x 16 B",
+            "algorithmic_bytes_per_frame": g_bytes, "ms_per_frame": g_ms,
+            "issued_16B_loads": {"per_frame": loads, "achieved_per_s": loads / (g_ms / 1e3), "peak_per_s": l1,
+                                 "frac": loads / (g_ms / 1e3) / l1},
+            "l2": {"achieved": g_ach, "peak": l2pk["gather_loads_per_s"] * 16 / 1e9, "unit": "GB/s",
+                   "frac": g_ach / (l2pk["gather_loads_per_s"] * 16 / 1e9),
+                   "peak_kind": "measured: scattered 16-byte loads from 32 MiB (nv_peak_gather) x 16 B"},
+            "hbm": {"achieved": hbm, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm / pk["hbm_gbs"],
+                    "peak_kind": pk_kind + " (copy)"}}
+
+
+def oracle_render_rate(net, params, cam, lut, opts, mu, shape, stride=10):
+    """The FP64 oracle renders every stride-th pixel of every stride-th row of the frame
+    (1920x1080 -> 192x108) with the network's parameters; returns (ms per full frame
+    extrapolated from the per-ray cost, threads, seconds, rays)."""
+    import oracle as O
+    W, H = cam["width"], cam["height"]
+    pix = np.array([py * W + px for py in range(stride // 2, H, stride) for px in range(stride // 2, W, stride)],
+                   np.int64)
+    onet = O.Net(L=net.L, F=net.F, log2T=net.log2T, Nmin=net.Nmin, b=net.b, dims=net.dims)
+    nz, ny, nx = shape
+    o = dict(opts, mc_cell=int(opts.get("mc_cell", 0)), dims=(nz, ny, nx))
+    t0 = time.perf_counter()
+    O.render_pixels(cam, lut, o, pix, net=onet, params=params, mumax=mu)
+    secs = time.perf_counter() - t0
+    return 1e3 * secs * (W * H) / len(pix), O.num_threads(), secs, len(pix)
+
+
+def bench_render_1080p(nv, I, CF, torch, frames, pk, pk_kind, l2pk, cpu=True):
+    """Config 3's frame as the metric's second half: the 1080p perspective march (0.5
+    voxel, 16^3 macrocells, ET 0.99, K 8) of a 512^3 blob volume through a T2^21 FP16
+    network trained with config 2's recipe (2000 steps of 2^18 points).  Median device
+    time of `frames` frames (the frame's input, the network and the volume already in
+    HBM); per-kernel times from the same frames with events around each kernel; the
+    rooflines of the gather (k_encode_tiles) and the tensor-core MLP (k_mlp_tc) in
+    inference; the raw-volume march of the same frame on the same GPU; image PSNR of
+    the neural frame against it; and the FP64 oracle's ms per frame from a 192x108
+    subsample of the rays on the host cores."""
+    cfg = CF.CFG3
+    c = cfg["net"]
+    D = cfg["volume"]
+    vt = I.blob_volume_torch(D, cfg["volume_seed"], "cuda")
+    lut, mu, opts = _render_setup(nv, I, torch, cfg, vt)
+    W, H = cfg["image"]
+    cam = I.perspective_camera(W, H, cfg["vfov"], cfg["eye"], cfg["target"])
+    mc = (mu, cfg["cell"], vt.shape)
+    r = nv.Renderer(W * H, K=cfg["K"])
+    raw, raw_ms = _time_render(r, torch, max(3, frames), cam=cam, lut=lut, opts=opts, raw=vt, mc=mc)
+    raw = raw.clone()
+    raw_it, raw_ns = r.stats()
+    net = nv.NeuralVolume(prec="fp16", **c.kwargs())
+    net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
+    for i in range(cfg["train_steps"]):
+        net.train_step(n=cfg["batch"], vol=vt, seed=11)
+    torch.cuda.synchronize()
+    img, ms = _time_render(r, torch, frames, cam=cam, lut=lut, opts=opts, net=net, mc=mc)
+    it, ns = r.stats()
+    psnr = _psnr(nv.image_mse(img, raw).item())
+    # per-kernel device times over the same frames
+    net.profile(True)
+    classes = ("encode", "mlp", "other", "render")
+    for k in classes:
+        net.profile_read(k)
+    for f in range(frames):
+        r.render(cam, lut, opts, net=net, mc=mc, out=img)
+    torch.cuda.synchronize()
+    kt = {k: net.profile_read(k) for k in classes}
+    net.profile(False)
+    per = {"k_encode_tiles": kt["encode"][0] / frames, "k_mlp_tc": kt["mlp"][0] / frames,
+           "k_coords": kt["other"][0] / frames, "k_composite": kt["render"][0] / frames}
+    launches = {k: v[1] // frames for k, v in kt.items()}
+    L, F, D0 = c.L, c.F, c.dims[0]
+    roof = gather_roofline(ns, per["k_encode_tiles"], L, F, D0, pk, pk_kind, l2pk)
+    roof["launches_per_frame"] = launches["encode"]
+    roof["traffic"] = None
+    roof["traffic_note"] = "see profiles/cfg3_render_launches.md (launch list; no DRAM counters in this line)"
+    m_ms = per["k_mlp_tc"]
+    flops = ns * 2 * (D0 * 64 + 64 * 64 + 64)
+    peak_t = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    out = {"workload": "cfg3: 512^3 blob volume, L16 F2 T2^21 FP16 network (2000 training steps), 1920x1080 "
+                       "perspective, step 0.5 voxel, 16^3 macrocells, ET 0.99, K 8",
+           "frame_ms": ms, "frames": frames, "iterations": it, "samples_per_frame": ns,
+           "decoded_samples_per_s": ns / (ms / 1e3), "image_psnr_db_vs_raw": psnr,
+           "raw_volume_frame_ms": raw_ms, "raw_iterations": raw_it, "raw_samples_per_frame": raw_ns,
+           "kernels_ms_per_frame": per, "launches_per_frame": launches,
+           "roofline": roof,
+           "mlp_tensor": {"kernel": "k_mlp_tc", "achieved": flops / (m_ms / 1e3) / 1e12, "peak": peak_t,
+                          "unit": "TFLOP/s", "frac": flops / (m_ms / 1e3) / 1e12 / peak_t,
+                          "algorithmic_flops_per_frame": flops, "ms_per_frame": m_ms,
+                          "peak_kind": pk_kind + " (bf16 sustained; the FP16 dense rate is the same)"}}
+    if cpu:
+        params = net.get_params().cpu().numpy()
+        o_ms, threads, secs, rays = oracle_render_rate(net, params, cam, lut.cpu().numpy(),
+                                                       dict(opts, mc_cell=cfg["cell"]), mu.cpu().numpy(),
+                                                       tuple(vt.shape))
+        out["cpu_baseline"] = {"value": o_ms, "unit": "ms/frame", "cores": threads, "kind": "oracle",
+                               "sample": f"FP64 oracle march of {rays} rays (every 10th pixel of every 10th row) "
+                                         f"through the same trained network, per-ray cost extrapolated to "
+                                         f"{W}x{H}", "seconds": secs}
+    net.close()
+    r.close()
+    del vt
+    torch.cuda.empty_cache()
+    return out
+
+
+def extra_cfg4_inloop(nv, I, CF, torch, pk, pk_kind, l2pk, frames=None):
     """Config 4: 1024^3 volume in HBM; each frame one 2^18-point training step and a
     1024x1024 render of the current FP16 network; ms/frame and the PSNR of the
     last frame against the raw-volume render."""
@@ -621,23 +799,54 @@ def extra_cfg4_inloop(nv, I, CF, torch, frames=None):
     net.set_online_macrocells(mm_on, vt.shape, cell)
     mc_on = (mu_on, cell, vt.shape)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    split = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(frames)]
     e0.record()
     for f in range(frames):
+        split[f][0].record()
         net.train_step(n=cfg["batch"], vol=vt, seed=21, loss_out=loss)
         nv.macrocells_mu(mm_on, vt.shape, cell, lut, out=mu_on)
+        split[f][1].record()
         r.render(cam, lut, opts, net=net, mc=mc_on, out=img)
+        split[f][2].record()
         if f % 100 == 99:
             psnr_curve.append((f + 1, nv.image_mse(img, raw)))
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / frames
+    train_ms = statistics.median(a.elapsed_time(b) for a, b, _ in split)
+    render_ms = statistics.median(b.elapsed_time(c2) for _, b, c2 in split)
+    # per-kernel times of the two halves, each profiled on its own over a few more frames
+    net.profile(True)
+    for k in ("encode", "mlp", "scatter", "adam", "other", "render"):
+        net.profile_read(k)
+    nprof = 5
+    for f in range(nprof):
+        net.train_step(n=cfg["batch"], vol=vt, seed=21, loss_out=loss)
+    torch.cuda.synchronize()
+    kt_train = {k: net.profile_read(k) for k in ("encode", "mlp", "scatter", "adam")}
+    for f in range(nprof):
+        r.render(cam, lut, opts, net=net, mc=mc_on, out=img)
+    torch.cuda.synchronize()
+    kt_render = {k: net.profile_read(k) for k in ("encode", "mlp", "other", "render")}
+    net.profile(False)
+    it, ns = r.stats()  # the last profiled frame's (the network no longer trains between them)
+    avg = {k: v[0] / v[1] for k, v in kt_train.items() if v[1]}
+    n_visit = net.adam_span()
+    train_roof = {k: roofline_of(k, avg, "fp16", pk, pk_kind, cfg["batch"], n_visit, net.n_table, c.dims, c.L,
+                                 c.F, l2pk) for k in ("encode", "mlp", "adam") if k in avg}
+    render_roof = gather_roofline(ns, kt_render["encode"][0] / nprof, c.L, c.F, c.dims[0], pk, pk_kind, l2pk)
     curve = [(f, _psnr(m.item())) for f, m in psnr_curve]
     # the last network rendered with ranges precomputed from the voxels instead
     img_pre = r.render(cam, lut, opts, net=net, mc=mc)
     psnr_pre = _psnr(nv.image_mse(img_pre, raw).item())
     cells_on = int((mu_on > 0).sum().item())
     cells_pre = int((mu > 0).sum().item())
-    out = {"frames": frames, "ms_per_frame": ms, "raw_ms": raw_ms, "psnr_db_by_frame": curve,
+    out = {"frames": frames, "ms_per_frame": ms, "train_ms_per_frame": train_ms, "render_ms_per_frame": render_ms,
+           "train_kernels_ms": {k: v[0] / nprof for k, v in kt_train.items()},
+           "render_kernels_ms": {k: v[0] / nprof for k, v in kt_render.items()},
+           "train_rooflines": train_roof, "render_roofline": render_roof,
+           "render_samples_per_frame": ns, "render_iterations": it,
+           "raw_ms": raw_ms, "psnr_db_by_frame": curve,
            "final_psnr_db": curve[-1][1] if curve else None, "n_params": net.n_params,
            "macrocells": "online (training samples)", "final_psnr_db_precomputed_macrocells": psnr_pre,
            "nonempty_cells_online": cells_on, "nonempty_cells_precomputed": cells_pre}
@@ -646,6 +855,24 @@ def extra_cfg4_inloop(nv, I, CF, torch, frames=None):
     del vt
     torch.cuda.empty_cache()
     return out
+
+
+def host_link_peak(torch, nbytes=1 << 30):
+    """GB/s of a pinned host -> device copy of nbytes (median of 5, CUDA events)."""
+    h = torch.empty(nbytes // 4, dtype=torch.float32).pin_memory()
+    d = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    d.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        d.copy_(h, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    del h, d
+    return nbytes / (statistics.median(ts) / 1e3) / 1e9
 
 
 def extra_cfg5_ooc(nv, I, CF, torch, steps=200, warm=10):
@@ -669,6 +896,7 @@ def extra_cfg5_ooc(nv, I, CF, torch, steps=200, warm=10):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     prep_s = time.perf_counter() - t0
+    link_peak = host_link_peak(torch)
     ring = nv.BrickRing(host, (D, D, D), B, cfg["ring"], seed=1)
     net = nv.NeuralVolume(prec="bf16", **c.kwargs())
     net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
@@ -700,7 +928,12 @@ def extra_cfg5_ooc(nv, I, CF, torch, steps=200, warm=10):
            "bytes_per_step": (b1 - b0) / steps, "host_link_gbs": (b1 - b0) / (c1 - c0) / 1e6 if c1 > c0 else None,
            "sustained_host_gbs": (b1 - b0) / (steps * ms) / 1e6, "final_loss": loss.item(),
            "psnr_db_256cube_subsample": psnr, "host_bytes": host.numel() * 4, "prep_s": prep_s,
-           "ring_bricks": cfg["ring"], "refresh_per_step": cfg["refresh"], "n_params": net.n_params}
+           "ring_bricks": cfg["ring"], "refresh_per_step": cfg["refresh"], "n_params": net.n_params,
+           "host_link_copy_peak_gbs": link_peak,
+           "host_link_peak_kind": "measured: 1 GiB pinned host -> device cudaMemcpyAsync, median of 5"}
+    if out["host_link_gbs"]:
+        out["host_link_frac"] = out["host_link_gbs"] / link_peak
+    out["sustained_host_frac"] = out["sustained_host_gbs"] / link_peak
     net.close()
     ring.close()
     del host, pts, sub
@@ -708,14 +941,17 @@ def extra_cfg5_ooc(nv, I, CF, torch, steps=200, warm=10):
     return out
 
 
-def run_extras(args):
+def run_extras(args, pk, pk_kind, l2pk):
+    import functools
+
     import torch
     from paper_2207_11620_gb300 import configs as CF
     from paper_2207_11620_gb300 import inputs as I
     from paper_2207_11620_gb300 import nv
     out = {}
+    cfg4 = functools.partial(extra_cfg4_inloop, pk=pk, pk_kind=pk_kind, l2pk=l2pk)
     for name, fn in (("cfg2_quality", extra_cfg2_quality), ("cfg3_render", extra_cfg3_render),
-                     ("cfg4_inloop", extra_cfg4_inloop), ("cfg5_ooc", extra_cfg5_ooc)):
+                     ("cfg4_inloop", cfg4), ("cfg5_ooc", extra_cfg5_ooc)):
         if name not in args.extras:
             continue
         clocks = Clocks(torch.cuda.current_device())

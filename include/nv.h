@@ -205,6 +205,38 @@ nv_status nv_sample(const nv_volume *vol, int64_t n, uint64_t seed, uint32_t ste
 nv_status nv_train_step(nv_ctx *ctx, const float *xyz_any, const float *target_any, int64_t n,
                         const nv_volume *vol, uint64_t seed, double *loss_dev);
 
+/* ---- data-parallel training (Sec. 4's training step split over replicas) ----- */
+
+/* One training step of Sec. 4 split over R replicas of the same network (one
+ * per GPU, same shape, parameters and optimizer state): replica r takes a
+ * disjoint shard of the global batch of n_total points; each runs
+ * nv_train_grad on its shard, the replicas reduce the buffers of
+ * nv_dp_buffers (the gradient by sum, the flags by maximum), and each then
+ * runs nv_optimizer_step: every replica applies the same update to the same
+ * parameters.  Sums of the shards' gradients equal the one-replica gradient of
+ * the whole batch up to FP32 summation order.
+ *
+ * nv_train_grad: forward, the loss chosen by nv_set_loss and backward of
+ * nv_train_step on this replica's shard (xyz_dev [n][3], target_dev [n],
+ * device memory; n may be 0), without the optimizer step: the gradient of the
+ * GLOBAL mean loss (the per-point upstream gradient divided by n_total, not n)
+ * is ADDED into NV_BUF_GRADS, and the shard's loss SUM (sum of (y - t)^2, or of
+ * |y - t| for L1) is WRITTEN to loss_sum_dev (one device double).  Online
+ * macrocells registered with the context are widened by the shard.
+ * NV_ERR_ARG if n > n_total or a pointer is host memory. */
+nv_status nv_train_grad(nv_ctx *ctx, const float *xyz_dev, const float *target_dev, int64_t n, int64_t n_total,
+                        double *loss_sum_dev);
+/* The device buffers a data-parallel step reduces across replicas, owned by
+ * the context: grads_dev [n] = NV_BUF_GRADS (reduce by sum) and flags_dev [2]
+ * int32 = (FP16 gradient overflow, a point outside [0,1]^3 was scattered)
+ * (reduce by maximum; every replica then skips the step, or leaves the
+ * reachable-block skipping, alike).  Unlike nv_buffer_ptr this keeps Adam's
+ * reachable-block skipping (nv_adam_span): the replicas' gradients are zero
+ * outside the reachable blocks, so their sum is.  Overwrite the buffers only
+ * with such reductions, on the context's stream order, before
+ * nv_optimizer_step. */
+nv_status nv_dp_buffers(nv_ctx *ctx, float **grads_dev, int64_t *n, int32_t **flags_dev);
+
 /* ---- out-of-core training samples (Sec. 4.1) ------------------------------- */
 
 /* A-17: a device ring of R bricks fed from a volume held in pinned host memory

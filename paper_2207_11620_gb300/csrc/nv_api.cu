@@ -29,14 +29,6 @@ nv_status nv_cuda_check(cudaError_t e, const char *what) {
 
 extern "C" const char *nv_last_error(void) { return g_err; }
 
-#define NV_TRY(x)                      \
-  do {                                 \
-    nv_status _s = (x);                \
-    if (_s != NV_OK) return _s;        \
-  } while (0)
-
-#define NV_CUDA(x, what) NV_TRY(nv_cuda_check((x), what))
-
 static bool is_host_ptr(const void *p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -91,6 +83,14 @@ static void ctx_free(nv_ctx *c) {
     if (c->batch_used[b]) cudaEventDestroy(c->batch_used[b]);
   }
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->enc_stream) {
+    cudaEventDestroy(c->enc_ready);
+    for (int b = 0; b < 2; ++b) {
+      cudaEventDestroy(c->enc_done[b]);
+      cudaEventDestroy(c->mlp_done[b]);
+    }
+    cudaStreamDestroy(c->enc_stream);
+  }
   cudaFree(c->tc_feat);
   cudaFree(c->tc_tgt);
   cudaFree(c->tc_xyz);
@@ -193,6 +193,7 @@ extern "C" nv_status nv_create(int L, int F, int log2T, int Nmin, double b, cons
 extern "C" nv_status nv_destroy(nv_ctx *c) {
   if (!c) return NV_OK;
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  if (c->enc_stream) cudaStreamSynchronize(c->enc_stream);
   cudaStreamSynchronize(c->stream);
   ctx_free(c);
   return NV_OK;
@@ -465,6 +466,50 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
   NV_TRY(launch_adam(c, 1.0 / (double)n, loss_dev));
   prof_end(c, NV_K_ADAM, tk);
   if (used_slot >= 0) NV_CUDA(cudaEventRecord(c->batch_used[used_slot], c->stream), "nv_train_step: record");
+  return NV_OK;
+}
+
+extern "C" nv_status nv_train_grad(nv_ctx *c, const float *xyz, const float *target, int64_t n, int64_t n_total,
+                                   double *loss_sum_dev) {
+  if (!c) return nv_fail(NV_ERR_ARG, "nv_train_grad: ctx is NULL");
+  if (n < 0 || n_total < 1 || n > n_total)
+    return nv_fail(NV_ERR_ARG, "nv_train_grad: need 0 <= n <= n_total, n_total >= 1 (n=%lld, n_total=%lld)",
+                   (long long)n, (long long)n_total);
+  if (n > 0 && (!xyz || !target)) return nv_fail(NV_ERR_ARG, "nv_train_grad: xyz and target are required");
+  if (n > 0 && (is_host_ptr(xyz) || is_host_ptr(target)))
+    return nv_fail(NV_ERR_ARG, "nv_train_grad: xyz and target must be device memory");
+  if (!loss_sum_dev || is_host_ptr(loss_sum_dev)) return nv_fail(NV_ERR_ARG, "nv_train_grad: loss_sum_dev must be device memory");
+  NV_CUDA(cudaMemsetAsync(loss_sum_dev, 0, sizeof(double), c->stream), "nv_train_grad: clear loss");
+  if (n == 0) return NV_OK;
+  MlpArgs a{};
+  a.n = n;
+  a.grads = c->grads;
+  a.ds = c->ds;
+  a.inv_n = (float)(1.0 / (double)n_total);  // the global batch mean
+  a.l1 = c->loss_kind == NV_LOSS_L1;
+  a.xyz = xyz;
+  a.in = target;
+  if (c->prec == NV_FP32) {
+    int tk = prof_begin(c);
+    NV_TRY(launch_mlp_f32_ext(c, MODE_TRAIN, a, nullptr, 1, n, loss_sum_dev));
+    prof_end(c, NV_K_MLP, tk);
+  } else {
+    NV_TRY(launch_mlp_tc_ext(c, MODE_TRAIN, a, nullptr, 1, n, loss_sum_dev));
+  }
+  if (c->mc_minmax) {
+    int tk = prof_begin(c);
+    NV_TRY(launch_mc_update(a.xyz, a.in, n, a.vol, a.seed, a.sample_step, c->mc_nx, c->mc_ny, c->mc_nz, c->mc_cell,
+                            c->mc_minmax, c->stream));
+    prof_end(c, NV_K_OTHER, tk);
+  }
+  return NV_OK;
+}
+
+extern "C" nv_status nv_dp_buffers(nv_ctx *c, float **grads_dev, int64_t *n, int32_t **flags_dev) {
+  if (!c || !grads_dev || !n || !flags_dev) return nv_fail(NV_ERR_ARG, "nv_dp_buffers: NULL argument");
+  *grads_dev = c->grads;
+  *n = c->n_params;
+  *flags_dev = &c->ds->overflow;  // [overflow, off_domain], adjacent in DevState
   return NV_OK;
 }
 

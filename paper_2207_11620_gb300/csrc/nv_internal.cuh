@@ -31,11 +31,12 @@ struct DevState {
   double loss_acc;    // sum of squared errors of the current batch
   double loss_mean;   // loss of the last training step (FP64)
   int step;           // optimizer steps taken (skipped overflow steps not counted)
+  // the two flags a data-parallel step reduces (maximum) across replicas, adjacent (nv_dp_buffers)
   int overflow;       // set when a gradient contribution was not finite
+  int off_domain;     // set (for good) when a table gradient was scattered from a point outside [0,1]^3
   float loss_scale;   // static loss scale of the tensor-core backward
   int err;            // set by a kernel whose bounded wait ran out
   unsigned adam_done; // CTAs of the running Adam launch that have finished (the last one resets it)
-  int off_domain;     // set (for good) when a table gradient was scattered from a point outside [0,1]^3
 };
 
 // Dense replicas of the coarsest levels' table gradient (tensor-core
@@ -84,6 +85,8 @@ struct nv_ctx {
   float *df_buf;                            // nv_backward with a coordinate gradient: dL/df [cap][L*F]
   int64_t df_cap;
   HotRep hot;                               // dense replicas of the coarsest levels' gradient (TC path)
+  cudaStream_t enc_stream;                  // TC training: gathers of the next part of a chunk (created on first use)
+  cudaEvent_t enc_ready, enc_done[2], mlp_done[2];
 };
 
 // Kernel timing hooks (nv_api.cu): bracket a launch on the context stream.
@@ -114,6 +117,15 @@ struct nv_renderer {
 // ---- error plumbing (defined in nv_api.cu) ----
 nv_status nv_fail(nv_status s, const char *fmt, ...);
 nv_status nv_cuda_check(cudaError_t e, const char *what);
+
+// Return a non-OK status from the enclosing function.
+#define NV_TRY(x)                      \
+  do {                                 \
+    nv_status _s = (x);                \
+    if (_s != NV_OK) return _s;        \
+  } while (0)
+
+#define NV_CUDA(x, what) NV_TRY(nv_cuda_check((x), what))
 
 // ---- device helpers ------------------------------------------------------
 

@@ -103,6 +103,8 @@ EXPORTS = {
                    C.c_void_p], C.c_int),
     "nv_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(Volume), C.c_uint64,
                        C.c_void_p], C.c_int),
+    "nv_train_grad": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p], C.c_int),
+    "nv_dp_buffers": ([C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_void_p)], C.c_int),
     "nv_macrocells_build": ([C.POINTER(Volume), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
                             C.c_int),
     "nv_renderer_create": ([C.c_int64, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
@@ -346,6 +348,27 @@ class NeuralVolume:
         else:
             v = volume(vol)
             _check(lib().nv_train_step(self._h, None, None, int(n), C.byref(v), int(seed), lp))
+
+    def train_grad(self, xyz, target, n_total, loss_sum=None):
+        """Forward, loss and backward of this replica's shard of a global batch of
+        n_total points (nv_train_grad): the global-mean gradient is added into the
+        gradient buffer, the shard's loss sum returned (one float64 on the device)."""
+        if loss_sum is None:
+            loss_sum = torch.zeros(1, dtype=torch.float64, device="cuda")
+        p, n = _points(xyz)
+        tp = _dev(target.contiguous(), name="target") if n else C.c_void_p()
+        _check(lib().nv_train_grad(self._h, p, tp, n, int(n_total), _dev(loss_sum, torch.float64, "loss_sum")))
+        return loss_sum
+
+    def dp_buffers(self):
+        """(gradient, flags): torch views (no copy) of the buffers a data-parallel step
+        reduces across replicas -- the FP32 gradient (sum) and the int32 (overflow,
+        off-domain) flags (maximum) (nv_dp_buffers)."""
+        g, n, f = C.c_void_p(), C.c_int64(), C.c_void_p()
+        _check(lib().nv_dp_buffers(self._h, C.byref(g), C.byref(n), C.byref(f)))
+        grads = torch.as_tensor(_CudaArray(g.value, n.value), device="cuda")
+        flags = torch.as_tensor(_CudaArray(f.value, 2, "<i4"), device="cuda")
+        return grads, flags
 
     def volume_mse(self, vol, out=None):
         if out is None:

@@ -1,12 +1,10 @@
-"""Replica runs on the GPUs of one node.
+"""Process-group plumbing of a run on the GPUs of one node (one process per GPU).
 
-The training step and the ray march shard by points and pixels with no
-exchange the method needs (Sec. 4 trains one network on one GPU), so a run on
-N GPUs is N independent replicas, one process per GPU: each rank trains its own
-network on its own points.  The ranks meet only at a barrier around the timed
-region and in a max-reduction of the timed interval; the whole-job throughput
-is the units all ranks processed over the slowest rank's time.  There is no
-data-path collective.
+The ranks join a process group, meet at a barrier around the timed region and
+take the max of their timed intervals; the whole-job throughput is the units
+all ranks processed over the slowest rank's time.  The training step itself is
+data parallel (dp.py): one network replicated on every rank, each rank on its
+own shard of the global batch, one all-reduce of the gradient per step.
 """
 from __future__ import annotations
 

@@ -36,25 +36,46 @@ def test_adam_roofline_counts_34_bytes_per_visited_parameter(bench):
     assert r32["algorithmic_bytes_per_launch"] == 32_000_000
 
 
-def test_mlp_roofline_reports_bytes_flops_and_reduction_rate(bench):
+def test_mlp_roofline_is_the_l2_scatter(bench):
     batch = 1 << 18
     avg = {"mlp": 0.15}
     r = bench.roofline_of("mlp", avg, "fp16", PK, "measured", batch, 1, 0, D, 16, 2, L2PK)
-    assert r["kernel"] == "k_mlp_tc" and r["bound"] == "hbm"
-    assert r["algorithmic_bytes_per_launch"] == batch * (2 * 32 + 4 + 8 * 16 * 2 * 4)
+    assert r["kernel"] == "k_mlp_tc" and r["bound"] == "l2" and r["unit"] == "GB/s"
+    # algorithmic bytes: the scatter's 8 corners x L x F FP32 reductions per point
+    assert r["algorithmic_bytes_per_launch"] == batch * 8 * 16 * 2 * 4
+    assert r["achieved"] == pytest.approx(batch * 1024 / 0.15e-3 / 1e9)
+    assert r["peak"] == pytest.approx(2e11 * 16 / 1e9)  # the measured reduction rate x 16 B
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["hbm"]["algorithmic_bytes_per_launch"] == batch * (2 * 32 + 4 + 8 * 16 * 2 * 4)
+    assert r["hbm"]["peak"] == 6000.0
     flops = 2 * batch * (32 * 64 + 64 * 64) + 2 * batch * (2 * 64 * 64 + 2 * 64 * 32)
     assert r["tensor"]["algorithmic_flops_per_launch"] == flops
     assert r["tensor"]["peak"] == 1500.0  # the sustained bf16 figure for a kernel inside a long step
-    sr = r["scatter_rate"]
+    sr = r["issued_16B_accesses"]
     assert sr["reductions_per_launch"] == batch * 16 * 6
     assert sr["frac"] == pytest.approx(sr["achieved_per_s"] / 2e11)
 
 
-def test_encode_roofline_reports_the_gather_rate(bench):
+def test_encode_roofline_is_the_l2_gather(bench):
     batch = 1 << 18
     r = bench.roofline_of("encode", {"encode": 0.07}, "fp16", PK, "measured", batch, 1, 0, D, 16, 2, L2PK)
-    assert r["algorithmic_bytes_per_launch"] == batch * (8 * 16 * 2 * 2 + 2 * 32 + 8 * 4 + 4)
-    assert r["gather_rate"]["loads_per_launch"] == batch * (16 * 5 + 8)
+    assert r["bound"] == "l2"
+    assert r["algorithmic_bytes_per_launch"] == batch * (8 * 16 * 2 * 2 + 8 * 4)
+    assert r["peak"] == pytest.approx(3e11 * 16 / 1e9)
+    assert r["hbm"]["algorithmic_bytes_per_launch"] == batch * (8 * 16 * 2 * 2 + 2 * 32 + 8 * 4 + 4)
+    assert r["issued_16B_accesses"]["loads_per_launch"] == batch * (16 * 5 + 8)
+
+
+def test_traffic_is_withheld_when_the_sources_changed(bench, tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "dram_traffic_cfg2.txt").write_text("# csrc_sha256 0000\nk_adam 123\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "csrc_digest", lambda: "0000")
+    assert bench.ncu_traffic("k_adam")[0] == 123
+    monkeypatch.setattr(bench, "csrc_digest", lambda: "1111")
+    val, note = bench.ncu_traffic("k_adam")
+    assert val is None and "changed" in note
 
 
 def test_fp32_mlp_is_an_alu_roofline(bench):

@@ -1,7 +1,7 @@
-"""The N-GPU run is N independent replicas (no data-path collective): the host
-logic -- process group, barrier, max of the timed interval, whole-job rate --
-checked with two gloo ranks on the CPU, and the reference arm's rule that only
-rank 0 reports."""
+"""The host logic of an N-GPU run -- process group, barrier, max of the timed
+interval, whole-job rate -- checked with two gloo ranks on the CPU, and the
+reference arm's rule that only rank 0 reports.  (The data-parallel step itself:
+tests/test_dp.py.)"""
 import os
 import socket
 import subprocess
