@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "fp16", "bf16"])
     ap.add_argument("--cpu-points", type=int, default=1 << 18, help="oracle sample size (points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="", choices=["", "render1080p"],
+    ap.add_argument("--case", default="", choices=["", "train_cfg2", "render1080p"],
                     help="run one profiling case instead of the benchmark")
     ap.add_argument("--extras", default="cfg2_quality,cfg3_render,cfg4_inloop,cfg5_ooc",
                     help="comma list of extra measurements (empty for none)")
@@ -722,15 +722,19 @@ def bench_render_1080p(nv, I, CF, torch, frames, pk, pk_kind, l2pk, cpu=True):
     img, ms = _time_render(r, torch, frames, cam=cam, lut=lut, opts=opts, net=net, mc=mc)
     it, ns = r.stats()
     psnr = _psnr(nv.image_mse(img, raw).item())
-    # per-kernel device times over the same frames
+    # per-kernel device times over the same frames, read after every frame (the
+    # library keeps at most 8192 timed launches between reads; a frame has ~800)
     net.profile(True)
     classes = ("encode", "mlp", "other", "render")
     for k in classes:
         net.profile_read(k)
+    kt = {k: [0.0, 0] for k in classes}
     for f in range(frames):
         r.render(cam, lut, opts, net=net, mc=mc, out=img)
-    torch.cuda.synchronize()
-    kt = {k: net.profile_read(k) for k in classes}
+        for k in classes:
+            t, n = net.profile_read(k)
+            kt[k][0] += t
+            kt[k][1] += n
     net.profile(False)
     per = {"k_encode_tiles": kt["encode"][0] / frames, "k_mlp_tc": kt["mlp"][0] / frames,
            "k_coords": kt["other"][0] / frames, "k_composite": kt["render"][0] / frames}
@@ -824,10 +828,13 @@ def extra_cfg4_inloop(nv, I, CF, torch, pk, pk_kind, l2pk, frames=None):
         net.train_step(n=cfg["batch"], vol=vt, seed=21, loss_out=loss)
     torch.cuda.synchronize()
     kt_train = {k: net.profile_read(k) for k in ("encode", "mlp", "scatter", "adam")}
-    for f in range(nprof):
+    kt_render = {k: [0.0, 0] for k in ("encode", "mlp", "other", "render")}
+    for f in range(nprof):  # read after every frame: at most 8192 timed launches are kept between reads
         r.render(cam, lut, opts, net=net, mc=mc_on, out=img)
-    torch.cuda.synchronize()
-    kt_render = {k: net.profile_read(k) for k in ("encode", "mlp", "other", "render")}
+        for k in kt_render:
+            t, n = net.profile_read(k)
+            kt_render[k][0] += t
+            kt_render[k][1] += n
     net.profile(False)
     it, ns = r.stats()  # the last profiled frame's (the network no longer trains between them)
     avg = {k: v[0] / v[1] for k, v in kt_train.items() if v[1]}
@@ -965,27 +972,55 @@ def run_extras(args, pk, pk_kind, l2pk):
 
 
 def run_case(args):
-    """Profiling case (for ncu captures): two 1080p frames of the config-3 geometry
-    with a random-weight FP16 network; prints one JSON line."""
+    """Profiling cases (for ncu captures); each prints one JSON line.
+
+    train_cfg2    args.warmup + args.steps config-2 training steps (FP16, 2^18 sampled points)
+    render1080p   the config-3 1080p frame of a trained FP16 network: 2000 training steps, one
+                  frame, then args.steps frames (and the timing helper's first call) in the NVTX
+                  range "frame"
+    The train case's last args.steps steps sit in the NVTX range "steps"."""
     import torch
     from paper_2207_11620_gb300 import build as B
     from paper_2207_11620_gb300 import configs as CF
     from paper_2207_11620_gb300 import inputs as I
     from paper_2207_11620_gb300 import nv
     B.build()
+    if args.case == "train_cfg2":
+        cfg = CF.CFG2
+        c = cfg["net"]
+        net = nv.NeuralVolume(prec="fp16", **c.kwargs())
+        net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
+        vol = torch.from_numpy(I.blob_volume(cfg["volume"], seed=cfg["volume_seed"])).cuda()
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for i in range(args.warmup):
+            net.train_step(n=cfg["batch"], vol=vol, seed=1000, loss_out=loss)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("steps")  # the launches a profiler capture selects
+        for i in range(args.steps):
+            net.train_step(n=cfg["batch"], vol=vol, seed=1000, loss_out=loss)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"case": args.case, "steps": args.warmup + args.steps, "loss": loss.item()}), flush=True)
+        return 0
     cfg = CF.CFG3
     c = cfg["net"]
     D = cfg["volume"]
     vt = I.blob_volume_torch(D, cfg["volume_seed"], "cuda")
     lut, mu, opts = _render_setup(nv, I, torch, cfg, vt)
     net = nv.NeuralVolume(prec="fp16", **c.kwargs())
-    p = I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims)
-    p[: net.n_table] = I.uniform_params(net.n_table, seed=6, scale=0.5)
-    net.set_params(p)
+    net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
+    for i in range(cfg["train_steps"]):
+        net.train_step(n=cfg["batch"], vol=vt, seed=11)
+    torch.cuda.synchronize()
     W, H = cfg["image"]
     cam = I.perspective_camera(W, H, cfg["vfov"], cfg["eye"], cfg["target"])
     r = nv.Renderer(W * H, K=cfg["K"])
-    img, ms = _time_render(r, torch, 1, cam=cam, lut=lut, opts=opts, net=net, mc=(mu, cfg["cell"], vt.shape))
+    mc = (mu, cfg["cell"], vt.shape)
+    r.render(cam, lut, opts, net=net, mc=mc)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("frame")  # the launches a profiler capture selects
+    img, ms = _median_frame_ms(torch, max(1, args.steps), lambda: r.render(cam, lut, opts, net=net, mc=mc))
+    torch.cuda.nvtx.range_pop()
     it, ns = r.stats()
     print(json.dumps({"case": args.case, "frame_ms": ms, "iterations": it, "samples": ns,
                       "mean_alpha": float(img[..., 3].mean())}), flush=True)

@@ -66,9 +66,9 @@ inline unsigned grid_for(int64_t items) { return (unsigned)((items + 255) / 256)
 
 // tgt (nullable): [cap] targets of a Philox training sample (ps.kind == 2);
 // xyz_out (nullable): [cap][3] its points, for the MLP kernel's scatter.
-// off_flag (nullable): set to 1 when a point lies outside [0,1]^3.
+// off_flag (nullable): set to 1 when a point lies outside [0,1]^3.  Launched on st.
 nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat,
-                              float *tgt, float *xyz_out, int *off_flag) {
+                              float *tgt, float *xyz_out, int *off_flag, cudaStream_t st) {
   const int C = c->nd.dims[0] / 8;
   const int64_t npad = (cs.cap + 127) & ~int64_t(127);
   if (npad == 0) return NV_OK;
@@ -77,12 +77,12 @@ nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSp
   const bool bf = c->prec == NV_BF16;
   switch (c->nd.F) {
     case 2:
-      if (bf) k_encode_tiles<2, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
-      else k_encode_tiles<2, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
+      if (bf) k_encode_tiles<2, true><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
+      else k_encode_tiles<2, false><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
       break;
     case 4:
-      if (bf) k_encode_tiles<4, true><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
-      else k_encode_tiles<4, false><<<g, 256, 0, c->stream>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
+      if (bf) k_encode_tiles<4, true><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
+      else k_encode_tiles<4, false><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
       break;
     default:
       return nv_fail(NV_ERR_UNSUPPORTED, "tensor-core encode: F=%d", c->nd.F);

@@ -83,14 +83,6 @@ static void ctx_free(nv_ctx *c) {
     if (c->batch_used[b]) cudaEventDestroy(c->batch_used[b]);
   }
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
-  if (c->enc_stream) {
-    cudaEventDestroy(c->enc_ready);
-    for (int b = 0; b < 2; ++b) {
-      cudaEventDestroy(c->enc_done[b]);
-      cudaEventDestroy(c->mlp_done[b]);
-    }
-    cudaStreamDestroy(c->enc_stream);
-  }
   cudaFree(c->tc_feat);
   cudaFree(c->tc_tgt);
   cudaFree(c->tc_xyz);
@@ -193,7 +185,6 @@ extern "C" nv_status nv_create(int L, int F, int log2T, int Nmin, double b, cons
 extern "C" nv_status nv_destroy(nv_ctx *c) {
   if (!c) return NV_OK;
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
-  if (c->enc_stream) cudaStreamSynchronize(c->enc_stream);
   cudaStreamSynchronize(c->stream);
   ctx_free(c);
   return NV_OK;

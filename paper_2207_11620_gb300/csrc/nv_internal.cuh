@@ -85,8 +85,6 @@ struct nv_ctx {
   float *df_buf;                            // nv_backward with a coordinate gradient: dL/df [cap][L*F]
   int64_t df_cap;
   HotRep hot;                               // dense replicas of the coarsest levels' gradient (TC path)
-  cudaStream_t enc_stream;                  // TC training: gathers of the next part of a chunk (created on first use)
-  cudaEvent_t enc_ready, enc_done[2], mlp_done[2];
 };
 
 // Kernel timing hooks (nv_api.cu): bracket a launch on the context stream.
