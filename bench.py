@@ -501,8 +501,11 @@ def _psnr(mse):
     return 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")
 
 
-def extra_cfg2_quality(nv, I, CF, torch, steps=1000):
-    """Config 2 as specified: 1000 steps of 2^18 points, FP32 vs FP16 MLP; volume PSNR."""
+def extra_cfg2_quality(nv, I, CF, torch, steps=1000, pk=None):
+    """Config 2 as specified: 1000 steps of 2^18 points, FP32 vs FP16 MLP; volume PSNR.
+    The FP32 path's step (one fused encode + MLP + scatter kernel on CUDA cores, then
+    Adam) is set against the CUDA cores' FP32 FMA rate: 152 SMs x 128 lanes x 2 FLOP x
+    the maximum SM clock."""
     cfg = CF.CFG2
     c = cfg["net"]
     vol = torch.from_numpy(I.blob_volume(cfg["volume"], seed=cfg["volume_seed"])).cuda()
@@ -520,6 +523,23 @@ def extra_cfg2_quality(nv, I, CF, torch, steps=1000):
         mse = net.volume_mse(vol).item()
         out[prec] = {"steps": steps, "ms_per_step": e0.elapsed_time(e1) / steps, "final_loss": loss.item(),
                      "volume_psnr_db": _psnr(mse)}
+        if prec == "fp32" and pk:
+            # the MLP kernel alone, timed with events over a few more steps
+            net.profile(True)
+            net.profile_read("mlp")
+            for i in range(20):
+                net.train_step(n=cfg["batch"], vol=vol, seed=31, loss_out=loss)
+            t, nl = net.profile_read("mlp")
+            net.profile(False)
+            ms = t / max(nl, 1)
+            D0 = c.dims[0]
+            flops = 2 * cfg["batch"] * (D0 * 64 + 64 * 64 + 64) + 2 * cfg["batch"] * (2 * 64 * 64 + 2 * 64 * D0 + 64)
+            peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            ach = flops / (ms / 1e3) / 1e12
+            out[prec]["roofline"] = {"kernel": "k_mlp_f32", "bound": "alu", "achieved": ach, "peak": peak,
+                                     "unit": "TFLOP/s", "frac": ach / peak, "avg_ms": ms,
+                                     "algorithmic_flops_per_launch": flops,
+                                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x max SM clock"}
         net.close()
     return out
 
@@ -957,7 +977,8 @@ def run_extras(args, pk, pk_kind, l2pk):
     from paper_2207_11620_gb300 import nv
     out = {}
     cfg4 = functools.partial(extra_cfg4_inloop, pk=pk, pk_kind=pk_kind, l2pk=l2pk)
-    for name, fn in (("cfg2_quality", extra_cfg2_quality), ("cfg3_render", extra_cfg3_render),
+    cfg2 = functools.partial(extra_cfg2_quality, pk=pk)
+    for name, fn in (("cfg2_quality", cfg2), ("cfg3_render", extra_cfg3_render),
                      ("cfg4_inloop", cfg4), ("cfg5_ooc", extra_cfg5_ooc)):
         if name not in args.extras:
             continue
