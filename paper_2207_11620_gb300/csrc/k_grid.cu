@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t
   const int64_t q = i - (int64_t)c * npad;
   uint8_t *dst = feat + (q >> 7) * (int64_t)(128 * D0 * 2) + tile_off((int)(q & 127), c * 8, D0);
   if (q >= n) {
-    if (q < npad) *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+    // rows past n in the last tile the MLP kernel reads are zeroed; tiles past it are never read
+    if (q < ((n + 127) & ~int64_t(127))) *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
     return;
   }
   const float3 x = point_at(ps, cs.off + q);

@@ -204,6 +204,10 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 
   const uint32_t sbase = tc::smem_u32(sm);
   const int64_t n = chunk_count(cs);
   const int64_t ntiles = (n + kTP - 1) / kTP;
+  // a CTA with no tile -- all of them for a chunk with no points, which the
+  // renderer launches for an upper bound of the live samples -- has nothing to
+  // do: leave before staging weights or tensor memory
+  if ((int64_t)blockIdx.x >= ntiles) return;
 
   // ---- stage the weights (FP16/BF16 shadow) as B operands ----
   const uint16_t *w0g = shadow + nd.n_table + nd.w_off[0];
