@@ -201,53 +201,91 @@ __global__ void k_raygen(nv_camera cam, float *ray, int *next_k, int64_t cap, in
 // Next K sample positions of each live ray (A-12, march_step).
 // seg_exp (non-NULL: adaptive step between step and step_max): the opacity
 // exponent of each emitted sample; next_k then holds the ray parameter t.
-__global__ void k_coords(const float *__restrict__ ray, int *next_k, int64_t cap, const int *count, int K,
-                         float step, float step_max, float alpha_exp, McView mc, float *coords, float *seg_exp,
-                         int *nvalid) {
+// A ray's K positions are contiguous (96 B at K = 8), so the positions are
+// staged in shared memory ([thread][3K + 1] floats) and each warp writes its 32
+// rays' block with coalesced stores: one store per sample from every thread hit
+// a different sector per lane and kept the load/store queue full.
+__global__ void __launch_bounds__(128) k_coords(const float *__restrict__ ray, int *next_k, int64_t cap,
+                                                const int *count, int K, float step, float step_max,
+                                                float alpha_exp, McView mc, float *coords, float *seg_exp,
+                                                int *nvalid) {
+  extern __shared__ float s_pos[];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *count) return;
-  const float o[3] = {ray[R_OX * cap + i], ray[R_OY * cap + i], ray[R_OZ * cap + i]};
-  const float d[3] = {ray[R_DX * cap + i], ray[R_DY * cap + i], ray[R_DZ * cap + i]};
-  const float t0 = ray[R_T0 * cap + i], t1 = ray[R_T1 * cap + i];
-  int k = next_k[i];
-  int cnt = 0;
-  float pos[3];
-  if (seg_exp) {
-    float t = __int_as_float(k);
-    while (cnt < K) {
-      float e;
-      const int m = march_step_adaptive(o, d, t1, step, step_max, alpha_exp, mc, t, pos, e);
-      if (m == kMarchEnd) break;
-      if (m == kMarchSkip) continue;
-      float *dst = coords + (i * K + cnt) * 3;
-      dst[0] = pos[0];
-      dst[1] = pos[1];
-      dst[2] = pos[2];
-      seg_exp[i * K + cnt] = e;
-      ++cnt;
+  const int n = *count;
+  const int stride = 3 * K + 1;  // odd: the per-thread rows fall in different banks
+  float *mine = s_pos + threadIdx.x * stride;
+  if (i < n) {
+    const float o[3] = {ray[R_OX * cap + i], ray[R_OY * cap + i], ray[R_OZ * cap + i]};
+    const float d[3] = {ray[R_DX * cap + i], ray[R_DY * cap + i], ray[R_DZ * cap + i]};
+    const float t0 = ray[R_T0 * cap + i], t1 = ray[R_T1 * cap + i];
+    int k = next_k[i];
+    int cnt = 0;
+    float pos[3];
+    if (seg_exp) {
+      float t = __int_as_float(k);
+      while (cnt < K) {
+        float e;
+        const int m = march_step_adaptive(o, d, t1, step, step_max, alpha_exp, mc, t, pos, e);
+        if (m == kMarchEnd) break;
+        if (m == kMarchSkip) continue;
+        mine[3 * cnt] = pos[0];
+        mine[3 * cnt + 1] = pos[1];
+        mine[3 * cnt + 2] = pos[2];
+        seg_exp[i * K + cnt] = e;
+        ++cnt;
+      }
+      k = __float_as_int(t);
+    } else {
+      while (cnt < K) {
+        const int m = march_step(o, d, t0, t1, step, mc, k, pos);
+        if (m == kMarchEnd) break;
+        if (m == kMarchSkip) continue;
+        mine[3 * cnt] = pos[0];
+        mine[3 * cnt + 1] = pos[1];
+        mine[3 * cnt + 2] = pos[2];
+        ++cnt;
+        ++k;
+      }
     }
-    k = __float_as_int(t);
+    for (int j = 3 * cnt; j < 3 * K; ++j) mine[j] = 0.f;
+    nvalid[i] = cnt;
+    next_k[i] = k;
+  }
+  __syncwarp();
+  // this warp's rays [w0, w0 + nr) are one contiguous block of nr * 3K floats
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = i - lane;
+  const int64_t left = (int64_t)n - w0;
+  const int nr = left < 0 ? 0 : (left > 32 ? 32 : (int)left);
+  const int per = 3 * K;
+  const float *wbase = s_pos + (threadIdx.x - lane) * stride;
+  float *dst = coords + w0 * per;
+  if ((per & 3) == 0) {  // K a multiple of 4: float4 stores (the block starts 16-byte aligned)
+    const int q = per / 4, nq = nr * q;
+    for (int f = lane; f < nq; f += 32) {
+      const int r = f / q, w = (f - r * q) * 4;
+      const float *src = wbase + r * stride + w;
+      reinterpret_cast<float4 *>(dst)[f] = make_float4(src[0], src[1], src[2], src[3]);
+    }
   } else {
-    while (cnt < K) {
-      const int m = march_step(o, d, t0, t1, step, mc, k, pos);
-      if (m == kMarchEnd) break;
-      if (m == kMarchSkip) continue;
-      float *dst = coords + (i * K + cnt) * 3;
-      dst[0] = pos[0];
-      dst[1] = pos[1];
-      dst[2] = pos[2];
-      ++cnt;
-      ++k;
+    const int nf = nr * per;
+    for (int f = lane; f < nf; f += 32) {
+      const int r = f / per;
+      dst[f] = wbase[r * stride + (f - r * per)];
     }
   }
-  for (int j = cnt; j < K; ++j) {
-    float *dst = coords + (i * K + j) * 3;
-    dst[0] = 0.f;
-    dst[1] = 0.f;
-    dst[2] = 0.f;
-  }
-  nvalid[i] = cnt;
-  next_k[i] = k;
+}
+
+// k_coords needs more than the default 48 KB of dynamic shared memory for K > 31
+// (the renderer allows K up to 64): raise its limit once.
+nv_status coords_kernel_setup() {
+  static int done = 0;
+  if (done) return NV_OK;
+  cudaError_t e = cudaFuncSetAttribute(k_coords, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((size_t)128 * (3 * 64 + 1) * sizeof(float)));
+  if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(k_coords)");
+  done = 1;
+  return NV_OK;
 }
 
 __global__ void k_values_raw(nv_volume v, const float *__restrict__ coords, const int *count, int K,
@@ -292,21 +330,35 @@ __global__ void k_composite(const float *__restrict__ ray, const int *__restrict
       as = aux[AUX_AS * cap + i];
     }
     bool done = false;
+    const float *vrow = values + i * K;  // this ray's K values, contiguous: read 4 at a time when K % 4 == 0
     if (as < 0.f) {  // the primary march (A-14)
-      for (int j = 0; j < nv; ++j) {
-        const float ex = seg_exp ? seg_exp[i * K + j] : alpha_exp;
-        float w;
-        const bool stop = composite_one(values[i * K + j], lut, ex, et, cr, cg, cb, ca, &w);
-        if (sh.on && w > bw) {
-          bw = w;
-          const float *p = coords + (i * K + j) * 3;
-          bp[0] = p[0];
-          bp[1] = p[1];
-          bp[2] = p[2];
+      for (int j0 = 0; j0 < nv && !done; j0 += 4) {
+        float vv[4];
+        if ((K & 3) == 0) {
+          const float4 t4 = *reinterpret_cast<const float4 *>(vrow + j0);
+          vv[0] = t4.x;
+          vv[1] = t4.y;
+          vv[2] = t4.z;
+          vv[3] = t4.w;
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) vv[u] = (j0 + u < nv) ? vrow[j0 + u] : 0.f;
         }
-        if (stop) {
-          done = true;
-          break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          if (j >= nv || done) break;
+          const float ex = seg_exp ? seg_exp[i * K + j] : alpha_exp;
+          float w;
+          const bool stop = composite_one(vv[u], lut, ex, et, cr, cg, cb, ca, &w);
+          if (sh.on && w > bw) {
+            bw = w;
+            const float *p = coords + (i * K + j) * 3;
+            bp[0] = p[0];
+            bp[1] = p[1];
+            bp[2] = p[2];
+          }
+          if (stop) done = true;
         }
       }
       if (nv < K) done = true;  // the ray left the volume during this batch
@@ -401,6 +453,9 @@ __global__ void k_scale_double(double *x, double s) { *x *= s; }
 
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
 
+// Dynamic shared memory of k_coords: 128 threads x (3K + 1) floats.
+inline size_t coords_smem(int K) { return (size_t)128 * (3 * K + 1) * sizeof(float); }
+
 }  // namespace
 
 nv_status launch_scale_double(double *x, double s, cudaStream_t st) {
@@ -466,6 +521,10 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   const int64_t cap = r->max_pixels;
   const int K = r->K;
   cudaStream_t st = net ? net->stream : r->stream;
+  {
+    const nv_status cs = coords_kernel_setup();
+    if (cs != NV_OK) return cs;
+  }
   cudaError_t e = cudaMemsetAsync(r->counters, 0, 2 * sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(r->d_samples, 0, sizeof(int64_t), st);
   if (e != cudaSuccess) return nv_cuda_check(e, "render memset");
@@ -500,7 +559,7 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   while (bound > 0 && issued < max_iter) {
     const int nxt = cur ^ 1;
     int tk = net ? prof_begin(net) : -1;
-    k_coords<<<blocks_for(bound, 128), 128, 0, st>>>(r->ray[cur], r->next_k[cur], cap, &r->counters[cur], K,
+    k_coords<<<blocks_for(bound, 128), 128, coords_smem(K), st>>>(r->ray[cur], r->next_k[cur], cap, &r->counters[cur], K,
                                                      o.step, o.step_max, o.alpha_exp, mv, r->coords, seg_exp,
                                                      r->nvalid);
     if (net) prof_end(net, NV_K_OTHER, tk);
@@ -570,6 +629,10 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
   const int64_t npix = (int64_t)cam.width * cam.height;
   const int64_t cap = r.max_pixels;
   const int K = r.K;
+  {
+    const nv_status cs = coords_kernel_setup();
+    if (cs != NV_OK) return cs;
+  }
   cudaError_t e = cudaMemsetAsync(r.counters, 0, 2 * sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(r.d_samples, 0, sizeof(int64_t), st);
   if (e != cudaSuccess) return nv_cuda_check(e, "render memset");
@@ -589,7 +652,7 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
     if (it >= max_iter) return nv_fail(NV_ERR_STATE, "ray march did not finish within %lld iterations", (long long)max_iter);
     const int nxt = cur ^ 1;
     const int64_t bound = live;
-    k_coords<<<blocks_for(bound, 128), 128, 0, st>>>(r.ray[cur], r.next_k[cur], cap, &r.counters[cur], K, o.step,
+    k_coords<<<blocks_for(bound, 128), 128, coords_smem(K), st>>>(r.ray[cur], r.next_k[cur], cap, &r.counters[cur], K, o.step,
                                                      0.f, o.alpha_exp, mv, r.coords, nullptr, r.nvalid);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_coords launch")) != NV_OK) return s;
     k_values_raw<<<blocks_for(bound * K, 256), 256, 0, st>>>(raw, r.coords, &r.counters[cur], K, r.values);
