@@ -181,16 +181,19 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ roofline ---
 
+# the sources the config-2 step's kernels (k_encode_tiles, k_mlp_tc, k_fold_replicas, k_adam) compile from
+STEP_SOURCES = ("k_grid.cu", "k_tc.cu", "k_adam.cu", "tc_grid.cuh", "tc_ptx.cuh", "nv_internal.cuh")
+
+
 def csrc_digest():
-    """SHA-256 over the library's CUDA sources (file names and contents, sorted)."""
+    """SHA-256 over the CUDA sources of the config-2 step's kernels (names and contents)."""
     import hashlib
     d = os.path.join(ROOT, "paper_2207_11620_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(name.encode())
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(f.read())
+    for name in STEP_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()
 
 
@@ -212,7 +215,7 @@ def ncu_traffic(kernel):
     if val is None:
         return None, "kernel not in the committed capture"
     if digest != csrc_digest():
-        return None, "kernel sources changed since the committed capture (profiles/dram_traffic_cfg2.txt)"
+        return None, "the step kernels' sources changed since the committed capture (profiles/dram_traffic_cfg2.txt)"
     return val, "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, committed capture " \
                 "(profiles/dram_traffic_cfg2.txt) of these sources"
 
