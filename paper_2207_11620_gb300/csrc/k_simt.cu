@@ -411,9 +411,15 @@ nv_status launch_encode_f32(const nv_ctx *c, const float *xyz, int64_t n, float 
   return nv_cuda_check(cudaGetLastError(), "k_encode_f32 launch");
 }
 
+// The register-blocked kernel for the D0 -> 64 -> 64 -> 1 networks (k_simt64.cu).
+bool f32x_supported(const NetDesc &nd);
+nv_status launch_mlp_f32x(const nv_ctx *c, int mode, const MlpArgs &a, const int *n_dev, int n_mult,
+                          int64_t n_upper, double *acc);
+
 // mode: MODE_INFER / MODE_BACKWARD / MODE_TRAIN, or 3 = volume MSE into acc.
 nv_status launch_mlp_f32_ext(const nv_ctx *c, int mode, const MlpArgs &a, const int *n_dev, int n_mult,
                              int64_t n_upper, double *acc) {
+  if (f32x_supported(c->nd)) return launch_mlp_f32x(c, mode, a, n_dev, n_mult, n_upper, acc);
   switch (mode) {
     case MODE_INFER: return dispatch_f<MODE_INFER>(c, a, n_dev, n_mult, n_upper, acc);
     case MODE_BACKWARD: return dispatch_f<MODE_BACKWARD>(c, a, n_dev, n_mult, n_upper, acc);
