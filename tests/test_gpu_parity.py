@@ -412,3 +412,23 @@ def test_peak_kernels_touch_every_access_in_bounds(nv):
     sink = torch.zeros(1024, dtype=torch.int32, device="cuda")
     nv.peak_gather(buf, ops, sink, seed=4)
     torch.cuda.synchronize()
+
+
+def test_fp32_generic_shape_matches_oracle(nv):
+    """A network outside the register-blocked FP32 kernel's shapes (hidden widths 32 and 16)
+    takes the generic one-point-per-thread kernel: forward and backward against the oracle."""
+    cfg = CF.NetCfg(4, 2, 12, 4, 1.6, (8, 32, 16, 1))
+    net = make_net(nv, cfg)
+    params = I.uniform_params(net.n_params, seed=21, scale=0.5)
+    net.set_params(params)
+    x = I.uniform_points(3000 + 17, seed=22)
+    got = net.infer(torch.from_numpy(x).cuda()).cpu().numpy()
+    want, wmag, _ = O.forward_mag(onet(cfg), params, x)
+    assert mag_err(got, want, wmag) <= FP32_TOL
+    x = x[kink_free(onet(cfg), params, x)]
+    dy = np.random.default_rng(23).normal(size=x.shape[0]).astype(np.float32)
+    g = torch.zeros(net.n_params, dtype=torch.float32, device="cuda")
+    net.backward(torch.from_numpy(x).cuda(), torch.from_numpy(dy).cuda(), g)
+    want = O.backward(onet(cfg), params, x, dy.astype(np.float64))
+    gmag = O.backward_mag(onet(cfg), params, x, np.abs(dy.astype(np.float64)))
+    assert mag_err(g.cpu().numpy(), want, gmag) <= FP32_TOL
