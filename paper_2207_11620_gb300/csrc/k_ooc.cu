@@ -88,28 +88,42 @@ __global__ void k_brick_sample(const float *__restrict__ ring, const int *__rest
   if (target) target[i] = c0 + wt[2] * (c1 - c0);
 }
 
-// Refresh copies: blockIdx.y picks the job (source brick -> destination slot),
-// blockIdx.x a contiguous part of the brick; 16-byte loads straight from the
-// pinned host bricks over the host link, four in flight per thread.
-__global__ void __launch_bounds__(256) k_brick_gather(const float4 *__restrict__ host, const int64_t *__restrict__ jobs,
-                                                      int count, int64_t brick_f4, float4 *ring) {
-  const int j = blockIdx.y;
-  const int64_t src = jobs[j], dst = jobs[count + j];
-  const float4 *s = host + src * brick_f4;
-  float4 *d = ring + dst * brick_f4;
-  const int64_t per = (brick_f4 + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = blockIdx.x * per, hi = min(brick_f4, lo + per);
-  for (int64_t i = lo + threadIdx.x; i < hi; i += 4 * blockDim.x) {
-    float4 v[4];
+// Refresh copies: a small persistent grid walks the (job, part) items -- job =
+// source brick -> destination slot, part = a contiguous eighth of the brick --
+// with 16-byte loads straight from the pinned host bricks over the host link,
+// four in flight per thread.  64 CTAs of 128 threads carry the link's rate
+// (256 bricks of 66^3 floats in 1.49 ms alone) and leave the SMs to the
+// training kernels that run meanwhile: on the 2048^3 ring workload a grid of one
+// 256-thread CTA per item ran after the training step rather than beside it
+// (2.9 + 1.4 -> 4.3 ms), 64 CTAs overlap it (3.1 ms), 16-32 starve the link and
+// 128-512 crowd the training kernels again.
+constexpr int kGatherThreads = 128;
+constexpr int kGatherCtas = 64;
+constexpr int kGatherParts = 8;
+
+__global__ void __launch_bounds__(kGatherThreads) k_brick_gather(const float4 *__restrict__ host,
+                                                                 const int64_t *__restrict__ jobs, int count,
+                                                                 int64_t brick_f4, float4 *ring) {
+  const int64_t items = (int64_t)count * kGatherParts;
+  const int64_t per = (brick_f4 + kGatherParts - 1) / kGatherParts;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int j = (int)(it / kGatherParts), q = (int)(it % kGatherParts);
+    const int64_t src = jobs[j], dst = jobs[count + j];
+    const float4 *s = host + src * brick_f4;
+    float4 *d = ring + dst * brick_f4;
+    const int64_t lo = q * per, hi = min(brick_f4, lo + per);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += 4 * blockDim.x) {
+      float4 v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t k = i + u * blockDim.x;
-      if (k < hi) v[u] = __ldcs(s + k);
-    }
+      for (int u = 0; u < 4; ++u) {
+        const int64_t k = i + u * blockDim.x;
+        if (k < hi) v[u] = __ldcs(s + k);
+      }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t k = i + u * blockDim.x;
-      if (k < hi) d[k] = v[u];
+      for (int u = 0; u < 4; ++u) {
+        const int64_t k = i + u * blockDim.x;
+        if (k < hi) d[k] = v[u];
+      }
     }
   }
 }
@@ -144,11 +158,11 @@ nv_status copy_slots(nv_ooc *o, int first, int count, uint64_t seed) {
   if (e != cudaSuccess) return nv_cuda_check(e, "nv_ooc: job list");
   // jobs[0..count) source bricks, jobs[count..2 count) destination slots
   const int64_t brick_f4 = o->brick_floats / 4;
-  const int parts = 8;
-  dim3 grid(parts, count);
+  const int64_t items = (int64_t)count * kGatherParts;
+  const unsigned grid = (unsigned)(items < kGatherCtas ? items : kGatherCtas);
   if (o->brick_floats % 4 == 0) {
-    k_brick_gather<<<grid, 256, 0, o->copy>>>(reinterpret_cast<const float4 *>(o->host_dev), jobs_dev, count,
-                                              brick_f4, reinterpret_cast<float4 *>(o->ring));
+    k_brick_gather<<<grid, kGatherThreads, 0, o->copy>>>(reinterpret_cast<const float4 *>(o->host_dev), jobs_dev,
+                                                         count, brick_f4, reinterpret_cast<float4 *>(o->ring));
     e = cudaGetLastError();
   } else {
     for (int k = 0; k < count && e == cudaSuccess; ++k)
