@@ -327,6 +327,16 @@ nv_status nv_renderer_destroy(nv_renderer *r);
 nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
                     const float *lut_dev, const nv_macrocells *mc, const nv_render_opts *opts,
                     float *rgba_dev);
+/* Image-tile split of nv_render (Sec. 5.2.1: each pixel's ray is marched and
+ * composited on its own, so a frame partitions by pixels with no exchange
+ * between the parts): rows [row0, row0 + rows) of the
+ * camera's image, each pixel's value equal to nv_render's, into rgba_dev
+ * [rows][width][4] (band-local).  0 <= row0, rows >= 1, row0 + rows <= height
+ * and width * rows <= the renderer's max_pixels, else NV_ERR_ARG.  Other
+ * arguments and errors as nv_render; nv_render_stats reports the band. */
+nv_status nv_render_rows(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
+                         const float *lut_dev, const nv_macrocells *mc, const nv_render_opts *opts, int row0,
+                         int rows, float *rgba_dev);
 /* In-shader inference (Sec. 5.1, App. A): the same ray march as nv_render on
  * the network `net`, as one kernel in which each thread owns a ray and the
  * network is evaluated inside the march -- a CTA of 128 rays gathers one

@@ -164,14 +164,15 @@ __device__ __forceinline__ int warp_append(int *counter, bool pred) {
 
 // next_k starts at sample 0, or, for the adaptive step, at the ray parameter t0
 // (float bits); aux (nullable) gets the initial single-shot shadow state.
-__global__ void k_raygen(nv_camera cam, float *ray, int *next_k, int64_t cap, int *count, float4 *rgba,
-                         bool adaptive, float *aux) {
+// Rows [row0, row0 + rows) of the image: pix indexes the band (row-major).
+__global__ void k_raygen(nv_camera cam, int row0, int rows, float *ray, int *next_k, int64_t cap, int *count,
+                         float4 *rgba, bool adaptive, float *aux) {
   const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t npix = (int64_t)cam.width * cam.height;
+  const int64_t npix = (int64_t)cam.width * rows;
   bool hit = false;
   float o[3], d[3], t0 = 0.f, t1 = 0.f;
   if (pix < npix) {
-    nv_camera_ray(cam, (int)(pix % cam.width), (int)(pix / cam.width), o, d);
+    nv_camera_ray(cam, (int)(pix % cam.width), row0 + (int)(pix / cam.width), o, d);
     hit = nv_box(o, d, t0, t1);
     if (!hit) rgba[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -516,8 +517,8 @@ nv_status launch_image_mse(const float *a, const float *b, int64_t n, double *ou
 }
 
 nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera &cam, const float *lut,
-                      const nv_macrocells *mc, const nv_render_opts &o, float *rgba) {
-  const int64_t npix = (int64_t)cam.width * cam.height;
+                      const nv_macrocells *mc, const nv_render_opts &o, int row0, int rows, float *rgba) {
+  const int64_t npix = (int64_t)cam.width * rows;
   const int64_t cap = r->max_pixels;
   const int K = r->K;
   cudaStream_t st = net ? net->stream : r->stream;
@@ -532,7 +533,7 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   const bool adaptive = o.step_max > 0.f;
   float *seg_exp = adaptive ? r->seg_exp : nullptr;
   ShadeArgs sh{o.shade, {o.light[0], o.light[1], o.light[2]}, o.ambient};
-  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r->ray[0], r->next_k[0], cap, &r->counters[0], out,
+  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, row0, rows, r->ray[0], r->next_k[0], cap, &r->counters[0], out,
                                                   adaptive, sh.on ? r->aux[0] : nullptr);
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
@@ -637,8 +638,8 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
   if (e == cudaSuccess) e = cudaMemsetAsync(r.d_samples, 0, sizeof(int64_t), st);
   if (e != cudaSuccess) return nv_cuda_check(e, "render memset");
   float4 *out = reinterpret_cast<float4 *>(rgba);
-  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, r.ray[0], r.next_k[0], cap, &r.counters[0], out, false,
-                                                  nullptr);
+  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, 0, cam.height, r.ray[0], r.next_k[0], cap, &r.counters[0],
+                                                  out, false, nullptr);
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
   const McView mv = mc_view(mc);

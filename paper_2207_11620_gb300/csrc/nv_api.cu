@@ -608,15 +608,16 @@ extern "C" nv_status nv_renderer_destroy(nv_renderer *r) {
   return NV_OK;
 }
 
-extern "C" nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
-                               const float *lut, const nv_macrocells *mc, const nv_render_opts *opts,
-                               float *rgba) {
+// Arguments of nv_render and nv_render_rows, whose image is `pixels` pixels.
+static nv_status check_render(const nv_renderer *r, const nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
+                              const float *lut, const nv_macrocells *mc, const nv_render_opts *opts,
+                              const float *rgba, int64_t pixels) {
   if (!r || !cam || !lut || !opts || !rgba) return nv_fail(NV_ERR_ARG, "nv_render: NULL argument");
   if (!net) NV_TRY(check_volume(raw, "nv_render"));
   if (net && !net->params_set) return nv_fail(NV_ERR_STATE, "nv_render: network parameters never set");
   if (cam->width < 1 || cam->height < 1) return nv_fail(NV_ERR_ARG, "nv_render: image %dx%d", cam->width, cam->height);
-  if ((int64_t)cam->width * cam->height > r->max_pixels)
-    return nv_fail(NV_ERR_ARG, "nv_render: %dx%d exceeds the renderer's %lld pixels", cam->width, cam->height,
+  if (pixels > r->max_pixels)
+    return nv_fail(NV_ERR_ARG, "nv_render: %lld pixels exceed the renderer's %lld", (long long)pixels,
                    (long long)r->max_pixels);
   if (!(opts->step > 0.f) || !(opts->alpha_exp > 0.f) || !(opts->et > 0.f))
     return nv_fail(NV_ERR_ARG, "nv_render: step, alpha_exp and et must be > 0");
@@ -632,7 +633,26 @@ extern "C" nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw
       return nv_fail(NV_ERR_ARG, "nv_render: shadows need a unit light direction and ambient in [0, 1]");
   }
   if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render: tan_half_fovy < 0");
-  return render_impl(r, net, raw, *cam, lut, mc, *opts, rgba);
+  return NV_OK;
+}
+
+extern "C" nv_status nv_render(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
+                               const float *lut, const nv_macrocells *mc, const nv_render_opts *opts,
+                               float *rgba) {
+  const int64_t pixels = cam ? (int64_t)cam->width * cam->height : 0;
+  NV_TRY(check_render(r, net, raw, cam, lut, mc, opts, rgba, pixels));
+  return render_impl(r, net, raw, *cam, lut, mc, *opts, 0, cam->height, rgba);
+}
+
+extern "C" nv_status nv_render_rows(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera *cam,
+                                    const float *lut, const nv_macrocells *mc, const nv_render_opts *opts,
+                                    int row0, int rows, float *rgba) {
+  if (cam && (rows < 1 || row0 < 0 || row0 > cam->height - rows))
+    return nv_fail(NV_ERR_ARG, "nv_render_rows: rows [%d, %d + %d) not inside the image's %d", row0, row0, rows,
+                   cam->height);
+  const int64_t pixels = cam ? (int64_t)cam->width * rows : 0;
+  NV_TRY(check_render(r, net, raw, cam, lut, mc, opts, rgba, pixels));
+  return render_impl(r, net, raw, *cam, lut, mc, *opts, row0, rows, rgba);
 }
 
 extern "C" nv_status nv_render_inshader(nv_ctx *net, const nv_camera *cam, const float *lut,

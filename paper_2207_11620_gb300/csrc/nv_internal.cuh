@@ -315,8 +315,10 @@ nv_status launch_sample(const nv_volume &v, int64_t n, uint64_t seed, uint32_t s
                         float *t, cudaStream_t s);
 nv_status launch_macrocells(const nv_volume &v, int cell, const float *lut, float *minmax,
                             float *mu, cudaStream_t s);
+// rows [row0, row0 + rows) of the camera's image into rgba [rows][width][4]
 nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const nv_camera &cam,
-                      const float *lut, const nv_macrocells *mc, const nv_render_opts &o, float *rgba);
+                      const float *lut, const nv_macrocells *mc, const nv_render_opts &o, int row0, int rows,
+                      float *rgba);
 // Online macrocells (k_render.cu): ranges reset to empty, widened by samples
 // (xyz == NULL: the Philox training sample of (seed, step) with its target from
 // vol), mu_max from the ranges.

@@ -19,6 +19,11 @@ Host-side orchestration only: the arithmetic runs in the library's kernels.  A
 replica is any object with train_grad(xyz, target, n_total) -> loss sum,
 dp_buffers() -> (gradient, flags) and optimizer_step() -- NeuralVolume on a
 GPU.
+
+Rendering splits by image rows (render_tiles): Sec. 5.2.1 marches and
+composites each pixel's ray on its own, so every rank renders its band of rows
+(nv_render_rows) with no exchange, and the bands are gathered only to assemble
+the frame.
 """
 from __future__ import annotations
 
@@ -65,3 +70,35 @@ class DataParallelStep:
         n_total = xyz.shape[0]
         lo, hi = shard(n_total, self.rank, self.world)
         return self.step_shard(xyz[lo:hi], target[lo:hi], n_total)
+
+
+def render_tiles(render_band, width: int, height: int, group=None):
+    """One frame split into row bands over the ranks of `group` (None: the
+    default group when one is initialised, else one rank renders everything).
+
+    render_band(row0, rows) renders rows [row0, row0 + rows) of the image and
+    returns them as a tensor [rows][width][4] (e.g. Renderer.render(..., rows=
+    (row0, rows))).  Rank r takes the rows shard(height, r, world); the bands
+    are all-gathered (padded to the largest band) so every rank returns the
+    whole image [height][width][4] on the device of its band."""
+    import torch
+    import torch.distributed as dist
+    d = dist if dist.is_available() and dist.is_initialized() else None
+    world = d.get_world_size(group) if d else 1
+    rank = d.get_rank(group) if d else 0
+    lo, hi = shard(height, rank, world)
+    band = render_band(lo, hi - lo) if hi > lo else None
+    if world == 1:
+        return band
+    most = -(-height // world)
+    dev = band.device if band is not None else ("cuda" if d.get_backend(group) == "nccl" else "cpu")
+    dtype = band.dtype if band is not None else torch.float32
+    buf = torch.zeros((most, width, 4), dtype=dtype, device=dev)
+    if band is not None:
+        if tuple(band.shape) != (hi - lo, width, 4):
+            raise ValueError(f"render_band({lo}, {hi - lo}) returned {tuple(band.shape)}")
+        buf[: hi - lo] = band
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    d.all_gather(parts, buf, group=group)
+    rows = [shard(height, r, world) for r in range(world)]
+    return torch.cat([parts[r][: b - a] for r, (a, b) in enumerate(rows)], dim=0)

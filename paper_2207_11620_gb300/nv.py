@@ -111,6 +111,8 @@ EXPORTS = {
     "nv_renderer_destroy": ([C.c_void_p], C.c_int),
     "nv_render": ([C.c_void_p, C.c_void_p, C.POINTER(Volume), C.POINTER(Camera), C.c_void_p,
                    C.POINTER(Macrocells), C.POINTER(RenderOpts), C.c_void_p], C.c_int),
+    "nv_render_rows": ([C.c_void_p, C.c_void_p, C.POINTER(Volume), C.POINTER(Camera), C.c_void_p,
+                        C.POINTER(Macrocells), C.POINTER(RenderOpts), C.c_int, C.c_int, C.c_void_p], C.c_int),
     "nv_render_stats": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64)], C.c_int),
     "nv_render_raw_noalloc": ([C.POINTER(Volume), C.POINTER(Camera), C.c_void_p, C.POINTER(Macrocells),
                                C.POINTER(RenderOpts), C.c_void_p, C.c_void_p], C.c_int),
@@ -434,12 +436,16 @@ class Renderer:
             pass
 
     def render(self, cam: dict, lut, opts: dict, net: NeuralVolume | None = None, raw=None,
-               mc: tuple | None = None, out=None):
+               mc: tuple | None = None, out=None, rows: tuple | None = None):
         """RGBA image [H, W, 4]; net=None renders the raw volume `raw`.
-        mc = (mu_max tensor, cell, raw volume shape (nz, ny, nx)) enables empty-space skipping."""
+        mc = (mu_max tensor, cell, raw volume shape (nz, ny, nx)) enables empty-space skipping.
+        rows = (row0, n): only image rows row0 .. row0 + n - 1, as an [n, W, 4] band (nv_render_rows)."""
         c = camera(cam)
+        h = c.height if rows is None else int(rows[1])
         if out is None:
-            out = torch.empty((c.height, c.width, 4), dtype=torch.float32, device="cuda")
+            out = torch.empty((h, c.width, 4), dtype=torch.float32, device="cuda")
+        elif out.numel() < h * c.width * 4:
+            raise ValueError(f"out holds {out.numel()} floats, the image needs {h * c.width * 4}")
         o = render_opts(opts, self.K)
         vp = C.byref(volume(raw)) if raw is not None else None
         mp = None
@@ -447,8 +453,13 @@ class Renderer:
             mu, cell, shape = mc
             m = Macrocells(_dev(mu, name="mu_max").value, int(cell), int(shape[2]), int(shape[1]), int(shape[0]))
             mp = C.byref(m)
-        _check(lib().nv_render(self._h, net.handle if net is not None else None, vp, C.byref(c),
-                               _dev(lut, name="lut"), mp, C.byref(o), _dev(out, name="out")))
+        nh = net.handle if net is not None else None
+        if rows is None:
+            _check(lib().nv_render(self._h, nh, vp, C.byref(c), _dev(lut, name="lut"), mp, C.byref(o),
+                                   _dev(out, name="out")))
+        else:
+            _check(lib().nv_render_rows(self._h, nh, vp, C.byref(c), _dev(lut, name="lut"), mp, C.byref(o),
+                                        int(rows[0]), int(rows[1]), _dev(out, name="out")))
         return out
 
     def render_pt(self, cam: dict, lut, opts: dict, mc: tuple, net: NeuralVolume | None = None, raw=None,

@@ -158,3 +158,62 @@ def test_one_process_needs_no_group():
     loss = float(step(torch.from_numpy(x), torch.from_numpy(t))[0])
     assert loss == pytest.approx(tr.step(x, t), rel=1e-12)
     np.testing.assert_allclose(rep.p, tr.params, rtol=1e-12, atol=1e-15)
+
+
+# ---- image tiles: a frame split by rows over the ranks (dp.render_tiles) ----
+
+def _tile_scene():
+    from paper_2207_11620_gb300 import inputs as I
+    vol = I.blob_volume(16, seed=2)
+    cam = I.perspective_camera(9, 7)  # 7 rows: bands of 4 / 3 and of 3 / 2 / 2
+    return vol, cam, I.ramp_lut(), dict(step=0.5 / 16, alpha_exp=0.5, et=0.99)
+
+
+def _oracle_band(vol, cam, lut, opts):
+    import oracle as O
+    W = cam["width"]
+
+    def band(row0, rows):
+        px = np.arange(row0 * W, (row0 + rows) * W)
+        return torch.from_numpy(O.render_pixels(cam, lut, opts, px, vol=vol).reshape(rows, W, 4))
+    return band
+
+
+def _tile_rank(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(ws), RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    vol, cam, lut, opts = _tile_scene()
+    calls = []
+    band = _oracle_band(vol, cam, lut, opts)
+
+    def counted(row0, rows):
+        calls.append((row0, rows))
+        return band(row0, rows)
+    img = dp.render_tiles(counted, cam["width"], cam["height"])
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, img.numpy(), calls))
+
+
+@pytest.mark.parametrize("ws", [2, 3])
+def test_gloo_ranks_render_the_frame_by_row_bands(ws):
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_tile_rank, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=300) for _ in range(ws)), key=lambda o: o[0])
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    vol, cam, lut, opts = _tile_scene()
+    W, H = cam["width"], cam["height"]
+    want = _oracle_band(vol, cam, lut, opts)(0, H).numpy()
+    assert (want[..., 3] > 0).mean() > 0.2
+    for r, img, calls in out:
+        assert calls == [(lo, hi - lo) for lo, hi in [dp.shard(H, r, ws)]]  # one band per rank, its own
+        assert np.array_equal(img, want)  # every rank holds the whole frame
