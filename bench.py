@@ -370,16 +370,17 @@ def run_ours(args):
             x, t = nv.sample(vol, batch, seed=1000 + rank, step=i)
             return dps.step_shard(x, t, ws * batch)
 
-        def step_host(hx, ht):
+        def step_host(hx, ht, loss_host=None):
             return dps.step_shard(hx.cuda(non_blocking=True), ht.cuda(non_blocking=True), ws * batch)
     else:
         def step(i):
             net.train_step(n=batch, vol=vol, seed=1000 + rank, loss_out=loss)
             return loss
 
-        def step_host(hx, ht):
-            net.train_step(hx, ht, loss_out=loss)
-            return loss
+        def step_host(hx, ht, loss_host=None):
+            # the step's last kernel writes the loss into the pinned host buffer
+            net.train_step(hx, ht, loss_out=loss if loss_host is None else loss_host)
+            return loss if loss_host is None else None
 
     for i in range(args.warmup):
         step(i)
@@ -418,7 +419,9 @@ def run_ours(args):
     from paper_2207_11620_gb300 import replicas
     value = replicas.job_throughput(ws, batch * args.steps, ms_max / 1e3)
 
-    # end to end through the C ABI: batches from pinned host memory, loss read back
+    # end to end through the C ABI: batches from pinned host memory, every step's loss
+    # written into pinned host memory by the step's last kernel (one GPU) or copied
+    # there from the device (data parallel)
     n_e2e = 4
     host_x, host_t = [], []
     for j in range(n_e2e):
@@ -434,8 +437,9 @@ def run_ours(args):
     t_wall = time.perf_counter()
     e0.record(stream)
     for i in range(args.steps):
-        lo = step_host(host_x[i % n_e2e], host_t[i % n_e2e])
-        loss_host.copy_(lo, non_blocking=True)
+        lo = step_host(host_x[i % n_e2e], host_t[i % n_e2e], loss_host)
+        if lo is not None:  # data parallel: the global loss is a device tensor
+            loss_host.copy_(lo, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall

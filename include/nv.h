@@ -201,7 +201,11 @@ nv_status nv_sample(const nv_volume *vol, int64_t n, uint64_t seed, uint32_t ste
  * overlaps the previous step's kernels; the host memory must stay unchanged until this step has completed,
  * e.g. until nv_sync) or both are NULL and the batch
  * is sampled from vol with nv_sample's generator at the context's sample
- * counter.  loss_dev (nullable): the batch loss before the update, FP64. */
+ * counter.  loss_dev (nullable): the batch loss before the update, FP64, in
+ * device memory or in pinned host memory (the kernel that ends the step writes
+ * it there over the host link, so a caller reading every step's loss needs no
+ * copy on the stream; the value is there once the step has completed).  Other
+ * host memory: NV_ERR_ARG. */
 nv_status nv_train_step(nv_ctx *ctx, const float *xyz_any, const float *target_any, int64_t n,
                         const nv_volume *vol, uint64_t seed, double *loss_dev);
 

@@ -38,6 +38,29 @@ static bool is_host_ptr(const void *p) {
   return at.type == cudaMemoryTypeUnregistered || at.type == cudaMemoryTypeHost;
 }
 
+// The address a kernel writes a result to: device memory as given, pinned
+// host memory through its device alias (the kernel writes it over the host
+// link, with no copy on the stream).  Pageable host memory is refused: no
+// kernel may write it.
+static nv_status kernel_out_ptr(double *p, double **out, const char *fn) {
+  *out = nullptr;
+  if (!p) return NV_OK;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nv_fail(NV_ERR_ARG, "%s: loss_dev is neither device nor pinned host memory", fn);
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    *out = p;
+    return NV_OK;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *out = static_cast<double *>(at.devicePointer);
+    return NV_OK;
+  }
+  return nv_fail(NV_ERR_ARG, "%s: loss_dev is neither device nor pinned host memory", fn);
+}
+
 struct Prof {
   static const int kMax = 8192;
   std::vector<cudaEvent_t> ev;   // 2 per recorded launch
@@ -388,6 +411,8 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
   if (n <= 0) return nv_fail(NV_ERR_ARG, "nv_train_step: n=%lld must be > 0", (long long)n);
   if ((xyz == nullptr) != (target == nullptr))
     return nv_fail(NV_ERR_ARG, "nv_train_step: give both xyz and target, or neither (sample from vol)");
+  double *loss_k = nullptr;
+  NV_TRY(kernel_out_ptr(loss_dev, &loss_k, "nv_train_step"));
   MlpArgs a{};
   a.n = n;
   a.grads = c->grads;
@@ -454,7 +479,7 @@ extern "C" nv_status nv_train_step(nv_ctx *c, const float *xyz, const float *tar
     prof_end(c, NV_K_OTHER, tk1);
   }
   int tk = prof_begin(c);
-  NV_TRY(launch_adam(c, 1.0 / (double)n, loss_dev));
+  NV_TRY(launch_adam(c, 1.0 / (double)n, loss_k));
   prof_end(c, NV_K_ADAM, tk);
   if (used_slot >= 0) NV_CUDA(cudaEventRecord(c->batch_used[used_slot], c->stream), "nv_train_step: record");
   return NV_OK;

@@ -169,6 +169,18 @@ def _dev(t, dtype=torch.float32, name="tensor"):
     return C.c_void_p(t.data_ptr())
 
 
+def _loss_ptr(t):
+    """nv_train_step's loss_dev: a CUDA float64 tensor, or a pinned CPU one (the
+    step's last kernel writes the loss there), or None."""
+    if t is None:
+        return C.c_void_p()
+    if t.is_cuda:
+        return _dev(t, torch.float64, "loss_out")
+    if t.dtype != torch.float64 or not t.is_pinned():
+        raise TypeError("loss_out must be a CUDA or a pinned CPU float64 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
 def _points(xyz):
     if xyz.dim() != 2 or xyz.shape[1] != 3:
         raise ValueError("points must be [n, 3]")
@@ -339,8 +351,9 @@ class NeuralVolume:
 
     def train_step(self, xyz=None, target=None, n=None, vol=None, seed=0, loss_out=None):
         """One step: on a given batch (device tensors or pinned/pageable host tensors), or
-        on n points sampled from `vol` (a CUDA [nz, ny, nx] tensor)."""
-        lp = _dev(loss_out, torch.float64, "loss_out") if loss_out is not None else C.c_void_p()
+        on n points sampled from `vol` (a CUDA [nz, ny, nx] tensor).  loss_out: one
+        float64, on the device or in pinned host memory (valid once the step is done)."""
+        lp = _loss_ptr(loss_out)
         if xyz is not None:
             for t in (xyz, target):
                 if t.dtype != torch.float32 or not t.is_contiguous():
