@@ -162,17 +162,35 @@ __device__ __forceinline__ int warp_append(int *counter, bool pred) {
   return base + __popc(mask & ((1u << lane) - 1u));
 }
 
+// Rays are generated in 8 x 4 pixel tiles, one warp per tile and the tiles in
+// row-major order, so a ray's slot neighbours are its image neighbours in both
+// directions: the 32 consecutive rays a gather CTA takes cover a compact patch,
+// and their samples share more table lines in L1 at the mid levels than a
+// 32-pixel row would.  Compaction appends a warp's survivors together, which
+// keeps the patches together in later iterations.
+constexpr int RG_TW = 8, RG_TH = 4;
+
+inline int64_t raygen_threads(int width, int rows) {
+  const int64_t tx = (width + RG_TW - 1) / RG_TW, ty = (rows + RG_TH - 1) / RG_TH;
+  return tx * ty * (RG_TW * RG_TH);
+}
+
 // next_k starts at sample 0, or, for the adaptive step, at the ray parameter t0
 // (float bits); aux (nullable) gets the initial single-shot shadow state.
 // Rows [row0, row0 + rows) of the image: pix indexes the band (row-major).
 __global__ void k_raygen(nv_camera cam, int row0, int rows, float *ray, int *next_k, int64_t cap, int *count,
                          float4 *rgba, bool adaptive, float *aux) {
-  const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t npix = (int64_t)cam.width * rows;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int tiles_x = (cam.width + RG_TW - 1) / RG_TW;
+  const int64_t tile = t / (RG_TW * RG_TH);
+  const int within = (int)(t % (RG_TW * RG_TH));
+  const int px = (int)(tile % tiles_x) * RG_TW + within % RG_TW;
+  const int64_t py = (tile / tiles_x) * RG_TH + within / RG_TW;
+  const int64_t pix = py * cam.width + px;
   bool hit = false;
   float o[3], d[3], t0 = 0.f, t1 = 0.f;
-  if (pix < npix) {
-    nv_camera_ray(cam, (int)(pix % cam.width), row0 + (int)(pix / cam.width), o, d);
+  if (px < cam.width && py < rows) {
+    nv_camera_ray(cam, px, row0 + (int)py, o, d);
     hit = nv_box(o, d, t0, t1);
     if (!hit) rgba[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -533,8 +551,8 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   const bool adaptive = o.step_max > 0.f;
   float *seg_exp = adaptive ? r->seg_exp : nullptr;
   ShadeArgs sh{o.shade, {o.light[0], o.light[1], o.light[2]}, o.ambient};
-  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, row0, rows, r->ray[0], r->next_k[0], cap, &r->counters[0], out,
-                                                  adaptive, sh.on ? r->aux[0] : nullptr);
+  k_raygen<<<blocks_for(raygen_threads(cam.width, rows), 256), 256, 0, st>>>(
+      cam, row0, rows, r->ray[0], r->next_k[0], cap, &r->counters[0], out, adaptive, sh.on ? r->aux[0] : nullptr);
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
 
@@ -627,7 +645,6 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
 // iteration is copied into a host stack variable and the stream synchronised.
 nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const nv_camera &cam, const float *lut,
                                const nv_macrocells *mc, const nv_render_opts &o, float *rgba, cudaStream_t st) {
-  const int64_t npix = (int64_t)cam.width * cam.height;
   const int64_t cap = r.max_pixels;
   const int K = r.K;
   {
@@ -638,8 +655,8 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
   if (e == cudaSuccess) e = cudaMemsetAsync(r.d_samples, 0, sizeof(int64_t), st);
   if (e != cudaSuccess) return nv_cuda_check(e, "render memset");
   float4 *out = reinterpret_cast<float4 *>(rgba);
-  k_raygen<<<blocks_for(npix, 256), 256, 0, st>>>(cam, 0, cam.height, r.ray[0], r.next_k[0], cap, &r.counters[0],
-                                                  out, false, nullptr);
+  k_raygen<<<blocks_for(raygen_threads(cam.width, cam.height), 256), 256, 0, st>>>(
+      cam, 0, cam.height, r.ray[0], r.next_k[0], cap, &r.counters[0], out, false, nullptr);
   nv_status s = nv_cuda_check(cudaGetLastError(), "k_raygen launch");
   if (s != NV_OK) return s;
   const McView mv = mc_view(mc);

@@ -321,18 +321,19 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 
     }
     if (wait_mma()) { failed = true; break; }
     uint32_t m1 = 0;  // ReLU mask of this thread's 32 columns of z1
+    {
+      // both halves of the thread's columns in flight before the one wait
+      float v[HH];
 #pragma unroll
-    for (int c = 0; c < HH / 16; ++c) {
-      float v[16];
-      tc::tmem_ld16(tD1 + lane_base + hh * HH + c * 16, v);
+      for (int c = 0; c < HH / 16; ++c) tc::tmem_ld16(tD1 + lane_base + hh * HH + c * 16, v + c * 16);
       tc::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (v[i] > 0.f) m1 |= 1u << (c * 16 + i);
+      for (int i = 0; i < HH; ++i) {
+        if (v[i] > 0.f) m1 |= 1u << i;
         v[i] = fmaxf(v[i], 0.f);
       }
-      st_row8<BF>(sm + P::A1, r, hh * (HH / 8) + 2 * c, kH, v);
-      st_row8<BF>(sm + P::A1, r, hh * (HH / 8) + 2 * c + 1, kH, v + 8);
+#pragma unroll
+      for (int c = 0; c < HH / 8; ++c) st_row8<BF>(sm + P::A1, r, hh * (HH / 8) + c, kH, v + c * 8);
     }
     tc::fence_before_sync();
     tc::fence_async_smem();
