@@ -16,7 +16,10 @@
 
 namespace {
 
-template <int F, bool BF>
+// CORNERS: every corner loaded on its own (gather_corners), for the coherent
+// sample batches of ray marches and voxel sweeps; otherwise the x-paired
+// gathers, whose fewer loads suit scattered points (training batches).
+template <int F, bool BF, bool CORNERS>
 __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t *__restrict__ shadow, PointSrc ps,
                                                       ChunkSpan cs, uint8_t *__restrict__ feat,
                                                       float *__restrict__ tgt, float *__restrict__ xyz_out,
@@ -47,7 +50,9 @@ __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t
     }
   }
   float f8[8];
-  if constexpr (F == 2) {
+  if constexpr (CORNERS) {
+    gather_corners<F, BF, 8 / F>(shadow, nd, c * (8 / F), x.x, x.y, x.z, f8);
+  } else if constexpr (F == 2) {
     gather_levels_f2<BF, 4>(shadow, nd, c * 4, x.x, x.y, x.z, f8);
   } else {  // one level at a time: fewer registers, more resident warps
 #pragma unroll
@@ -67,26 +72,40 @@ inline unsigned grid_for(int64_t items) { return (unsigned)((items + 255) / 256)
 
 // tgt (nullable): [cap] targets of a Philox training sample (ps.kind == 2);
 // xyz_out (nullable): [cap][3] its points, for the MLP kernel's scatter.
-// off_flag (nullable): set to 1 when a point lies outside [0,1]^3.  Launched on st.
+// off_flag (nullable): set to 1 when a point lies outside [0,1]^3.  coherent:
+// neighbouring points share most corners (ray-march samples, voxel centres).
+// Launched on st.
 nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat,
-                              float *tgt, float *xyz_out, int *off_flag, cudaStream_t st) {
+                              float *tgt, float *xyz_out, int *off_flag, bool coherent, cudaStream_t st) {
   const int C = c->nd.dims[0] / 8;
   const int64_t npad = (cs.cap + 127) & ~int64_t(127);
   if (npad == 0) return NV_OK;
   const uint16_t *sh = reinterpret_cast<const uint16_t *>(c->shadow);
   const unsigned g = grid_for(npad * C);
   const bool bf = c->prec == NV_BF16;
+#define NV_ENC(F_, BF_, CO_) k_encode_tiles<F_, BF_, CO_><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag)
   switch (c->nd.F) {
     case 2:
-      if (bf) k_encode_tiles<2, true><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
-      else k_encode_tiles<2, false><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
+      if (coherent) {
+        if (bf) NV_ENC(2, true, true);
+        else NV_ENC(2, false, true);
+      } else {
+        if (bf) NV_ENC(2, true, false);
+        else NV_ENC(2, false, false);
+      }
       break;
     case 4:
-      if (bf) k_encode_tiles<4, true><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
-      else k_encode_tiles<4, false><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag);
+      if (coherent) {
+        if (bf) NV_ENC(4, true, true);
+        else NV_ENC(4, false, true);
+      } else {
+        if (bf) NV_ENC(4, true, false);
+        else NV_ENC(4, false, false);
+      }
       break;
     default:
       return nv_fail(NV_ERR_UNSUPPORTED, "tensor-core encode: F=%d", c->nd.F);
   }
+#undef NV_ENC
   return nv_cuda_check(cudaGetLastError(), "k_encode_tiles launch");
 }

@@ -588,6 +588,7 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
       a.xyz = r->coords;
       a.y = r->values;
       a.ds = net->ds;
+      a.coherent = 1;
       s = (net->prec == NV_FP32)
               ? launch_mlp_f32_ext(net, MODE_INFER, a, &r->counters[cur], K, bound * K, nullptr)
               : launch_mlp_tc_ext(net, MODE_INFER, a, &r->counters[cur], K, bound * K, nullptr);

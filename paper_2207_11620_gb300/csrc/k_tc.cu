@@ -34,7 +34,7 @@
 #include "tc_ptx.cuh"
 
 nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSpan &cs, uint8_t *feat,
-                              float *tgt, float *xyz_out, int *off_flag, cudaStream_t st);
+                              float *tgt, float *xyz_out, int *off_flag, bool coherent, cudaStream_t st);
 
 namespace {
 
@@ -704,7 +704,8 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
   for (int64_t off = 0; off < n_upper; off += c->tc_cap) {
     ChunkSpan cs{n_dev, n_mult, a.n, off, n_upper - off < c->tc_cap ? n_upper - off : c->tc_cap};
     int tk = prof_begin(c);
-    s = launch_encode_tiles(c, ps, cs, c->tc_feat, tgt, xyz_out, off_flag, c->stream);
+    s = launch_encode_tiles(c, ps, cs, c->tc_feat, tgt, xyz_out, off_flag, a.coherent != 0 || mode == 3,
+                            c->stream);
     prof_end(c, NV_K_ENCODE, tk);
     if (s != NV_OK) return s;
     tk = prof_begin(c);

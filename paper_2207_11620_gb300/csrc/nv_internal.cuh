@@ -286,6 +286,7 @@ struct MlpArgs {
   int l1;                // TRAIN: L1 loss (else L2)
   float *df_out;         // BACKWARD (nullable): dL/df of every point, [n][L*F] FP32
   HotRep hot;            // TRAIN / BACKWARD, tensor-core path (levels = 0: none)
+  int coherent;          // INFER: the points are ray-march samples (neighbours share corners)
 };
 
 // FP32 CUDA-core path

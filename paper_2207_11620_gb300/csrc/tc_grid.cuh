@@ -141,6 +141,19 @@ __device__ __forceinline__ void unpack16(const T &u, float *e) {
   }
 }
 
+// Weights of the x-corners of corner row q (dy = q & 1, dz = q >> 1) and the
+// row's contribution, every operation rounded on its own: all gathers below
+// blend in this order, so they give the same features bit for bit whatever
+// loads they use.
+__device__ __forceinline__ void row_weights(int q, float wx, float wy, float wz, float &w0, float &w1) {
+  const float wyz = __fmul_rn((q & 1) ? wy : __fsub_rn(1.f, wy), (q >> 1) ? wz : __fsub_rn(1.f, wz));
+  w0 = __fmul_rn(__fsub_rn(1.f, wx), wyz);
+  w1 = __fmul_rn(wx, wyz);
+}
+__device__ __forceinline__ float blend2(float acc, float w0, float v0, float w1, float v1) {
+  return __fadd_rn(acc, __fmaf_rn(w0, v0, __fmul_rn(w1, v1)));
+}
+
 // A-1..A-3 for G consecutive levels, x-paired: corners (cx, .) and (cx + 1, .)
 // hash to entries h and h ^ 1 when cx is even (the x prime is 1), so one
 // aligned 2-entry load serves both; for odd cx the second corner is loaded
@@ -155,23 +168,21 @@ __device__ __forceinline__ void gather_levels(const uint16_t *__restrict__ shado
   PT pr[G][4];
   ST sg[G][4];
   uint32_t odd0 = 0, evenm = 0;
-  float wxs[G], wyzs[G][4];
+  float wxs[G], wys[G], wzs[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const int l = l0 + g;
     int cx, cy, cz;
-    float wy, wz;
     const float N = (float)nd.res[l];
     nv_cell(x, N, cx, wxs[g]);
-    nv_cell(y, N, cy, wy);
-    nv_cell(z, N, cz, wz);
+    nv_cell(y, N, cy, wys[g]);
+    nv_cell(z, N, cz, wzs[g]);
     const bool even = (cx & 1) == 0;
     if (even) evenm |= 1u << g;
     const uint16_t *tab = shadow + (size_t)l * nd.T * F;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int dy = q & 1, dz = q >> 1;
-      wyzs[g][q] = (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
       const uint32_t hy = ((uint32_t)(cy + dy) * 2654435761u) ^ ((uint32_t)(cz + dz) * 805459861u);
       const uint32_t h0 = ((uint32_t)cx ^ hy) & mask;
       if (h0 & 1u) odd0 |= 1u << (g * 4 + q);
@@ -198,9 +209,10 @@ __device__ __forceinline__ void gather_levels(const uint16_t *__restrict__ shado
       } else {
         unpack16<F, BF>(sg[g][q], e1);
       }
-      const float w0 = (1.f - wxs[g]) * wyzs[g][q], w1 = wxs[g] * wyzs[g][q];
+      float w0, w1;
+      row_weights(q, wxs[g], wys[g], wzs[g], w0, w1);
 #pragma unroll
-      for (int j = 0; j < F; ++j) acc[j] += w0 * pv[o0 + j] + w1 * e1[j];
+      for (int j = 0; j < F; ++j) acc[j] = blend2(acc[j], w0, pv[o0 + j], w1, e1[j]);
     }
 #pragma unroll
     for (int j = 0; j < F; ++j) out[g * F + j] = acc[j];
@@ -270,19 +282,71 @@ __device__ __forceinline__ void gather_levels_f2(const uint16_t *__restrict__ sh
     float a0 = 0.f, a1 = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int dy = q & 1, dz = q >> 1;
       const uint32_t s = sel[g] >> (8 * q);
       const uint32_t e0 = pick4(grp[g][q], s & 3u);
       const uint32_t e1 = (s & 16u) ? pick4(grp[g][q], (s >> 2) & 3u) : sg[g][q];
       const float2 v0 = Half<BF>::unpack(*reinterpret_cast<const typename Half<BF>::T2 *>(&e0));
       const float2 v1 = Half<BF>::unpack(*reinterpret_cast<const typename Half<BF>::T2 *>(&e1));
-      const float wyz = (dy ? wys[g] : 1.f - wys[g]) * (dz ? wzs[g] : 1.f - wzs[g]);
-      const float w0 = (1.f - wxs[g]) * wyz, w1 = wxs[g] * wyz;
-      a0 += w0 * v0.x + w1 * v1.x;
-      a1 += w0 * v0.y + w1 * v1.y;
+      float w0, w1;
+      row_weights(q, wxs[g], wys[g], wzs[g], w0, w1);
+      a0 = blend2(a0, w0, v0.x, w1, v1.x);
+      a1 = blend2(a1, w0, v0.y, w1, v1.y);
     }
     out[2 * g] = a0;
     out[2 * g + 1] = a1;
+  }
+}
+
+// A-1..A-3 for G consecutive levels with each of the 8 corners loaded on its
+// own (8 one-entry loads per level, no selection among loaded entries).  For
+// the sample batches of a ray march -- the K samples of a ray in adjacent work
+// items, neighbouring rays in neighbouring items -- most corner loads hit in
+// L1 and the x-paired gathers above are bound by the integer work of picking
+// entries out of their 16-byte groups, not by memory; this one issues a third
+// as many instructions per level.  The hash of corner (cx + dx, cy + dy, cz +
+// dz) is formed from the per-axis products (cy + 1) P1 = cy P1 + P1 (mod 2^32).
+template <int F, bool BF, int G>
+__device__ __forceinline__ void gather_corners(const uint16_t *__restrict__ shadow, const NetDesc &nd, int l0,
+                                               float x, float y, float z, float *out) {
+  using ST = typename Raw<F>::S;
+  const uint32_t mask = nd.T - 1;
+  ST e[G][8];
+  float wxs[G], wys[G], wzs[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int l = l0 + g;
+    int cx, cy, cz;
+    const float N = (float)nd.res[l];
+    nv_cell(x, N, cx, wxs[g]);
+    nv_cell(y, N, cy, wys[g]);
+    nv_cell(z, N, cz, wzs[g]);
+    const ST *tab = reinterpret_cast<const ST *>(shadow + (size_t)l * nd.T * F);
+    const uint32_t y0 = (uint32_t)cy * 2654435761u, y1 = y0 + 2654435761u;
+    const uint32_t z0 = (uint32_t)cz * 805459861u, z1 = z0 + 805459861u;
+    const uint32_t x0 = (uint32_t)cx, x1 = x0 + 1u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t hy = ((q & 1) ? y1 : y0) ^ ((q >> 1) ? z1 : z0);
+      e[g][2 * q] = __ldg(tab + ((x0 ^ hy) & mask));
+      e[g][2 * q + 1] = __ldg(tab + ((x1 ^ hy) & mask));
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    float acc[F];
+#pragma unroll
+    for (int j = 0; j < F; ++j) acc[j] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v0[F], v1[F], w0, w1;
+      unpack16<F, BF>(e[g][2 * q], v0);
+      unpack16<F, BF>(e[g][2 * q + 1], v1);
+      row_weights(q, wxs[g], wys[g], wzs[g], w0, w1);
+#pragma unroll
+      for (int j = 0; j < F; ++j) acc[j] = blend2(acc[j], w0, v0[j], w1, v1[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < F; ++j) out[g * F + j] = acc[j];
   }
 }
 
