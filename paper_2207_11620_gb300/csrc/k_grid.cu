@@ -8,9 +8,10 @@
 // kernel's backward epilogue (k_tc.cu).
 //
 // Work item = (point, chunk of 8 features): with F features per level a chunk
-// covers 8 / F levels.  Items are chunk-major, so neighbouring threads handle
-// neighbouring points at the same levels (coarse-level table lines are shared
-// in L1) and write one 16-byte core-matrix row each.
+// covers 8 / F levels.  The grid's y index is the chunk and its x index runs
+// over points, so neighbouring threads handle neighbouring points at the same
+// levels (coarse-level table lines are shared in L1) and write one 16-byte
+// core-matrix row each.
 #include "nv_internal.cuh"
 #include "tc_grid.cuh"
 
@@ -20,18 +21,16 @@ namespace {
 // sample batches of ray marches and voxel sweeps; otherwise the x-paired
 // gathers, whose fewer loads suit scattered points (training batches).
 template <int F, bool BF, bool CORNERS>
-__global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t *__restrict__ shadow, PointSrc ps,
+__global__ void __launch_bounds__(256, CORNERS ? 6 : 5) k_encode_tiles(NetDesc nd, const uint16_t *__restrict__ shadow, PointSrc ps,
                                                       ChunkSpan cs, uint8_t *__restrict__ feat,
                                                       float *__restrict__ tgt, float *__restrict__ xyz_out,
                                                       int *off_flag) {
   const int D0 = nd.dims[0];
-  const int C = D0 / 8;
   const int64_t n = chunk_count(cs);
   const int64_t npad = (cs.cap + 127) & ~int64_t(127);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npad * C) return;
-  const int c = (int)(i / npad);
-  const int64_t q = i - (int64_t)c * npad;
+  const int c = blockIdx.y;  // the chunk of 8 features
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= npad) return;
   uint8_t *dst = feat + (q >> 7) * (int64_t)(128 * D0 * 2) + tile_off((int)(q & 127), c * 8, D0);
   if (q >= n) {
     // rows past n in the last tile the MLP kernel reads are zeroed; tiles past it are never read
@@ -66,7 +65,7 @@ __global__ void __launch_bounds__(256) k_encode_tiles(NetDesc nd, const uint16_t
   *reinterpret_cast<uint4 *>(dst) = u;
 }
 
-inline unsigned grid_for(int64_t items) { return (unsigned)((items + 255) / 256); }
+inline dim3 grid_for(int64_t points, int chunks) { return dim3((unsigned)((points + 255) / 256), (unsigned)chunks); }
 
 }  // namespace
 
@@ -81,7 +80,7 @@ nv_status launch_encode_tiles(const nv_ctx *c, const PointSrc &ps, const ChunkSp
   const int64_t npad = (cs.cap + 127) & ~int64_t(127);
   if (npad == 0) return NV_OK;
   const uint16_t *sh = reinterpret_cast<const uint16_t *>(c->shadow);
-  const unsigned g = grid_for(npad * C);
+  const dim3 g = grid_for(npad, C);
   const bool bf = c->prec == NV_BF16;
 #define NV_ENC(F_, BF_, CO_) k_encode_tiles<F_, BF_, CO_><<<g, 256, 0, st>>>(c->nd, sh, ps, cs, feat, tgt, xyz_out, off_flag)
   switch (c->nd.F) {

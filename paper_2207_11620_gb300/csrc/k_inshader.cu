@@ -129,8 +129,7 @@ __global__ void __launch_bounds__(kTP) k_render_is(NetDesc nd, const float *__re
       uint4 u = make_uint4(0u, 0u, 0u, 0u);
       if (live) {
         float f8[8];
-        if constexpr (F == 2) gather_levels_f2<BF, 4>(shadow, nd, c * 4, pos[0], pos[1], pos[2], f8);
-        else gather_levels<F, BF, 8 / F>(shadow, nd, c * (8 / F), pos[0], pos[1], pos[2], f8);
+        gather_corners<F, BF, 8 / F>(shadow, nd, c * (8 / F), pos[0], pos[1], pos[2], f8);
         u.x = pack16x2<BF>(f8[0], f8[1]);
         u.y = pack16x2<BF>(f8[2], f8[3]);
         u.z = pack16x2<BF>(f8[4], f8[5]);
@@ -151,14 +150,13 @@ __global__ void __launch_bounds__(kTP) k_render_is(NetDesc nd, const float *__re
     }
     if (wait_mma()) { failed = true; break; }
 #pragma unroll
-    for (int c = 0; c < kH / 16; ++c) {
-      float v[16];
-      tc::tmem_ld16(tD1 + lane_base + c * 16, v);
+    for (int c = 0; c < kH / 32; ++c) {  // 32 columns in flight per wait
+      float v[32];
+      tc::tmem_ld16(tD1 + lane_base + c * 32, v);
+      tc::tmem_ld16(tD1 + lane_base + c * 32 + 16, v + 16);
       tc::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-      st_row8<BF>(sm + P::A1, tid, 2 * c, kH, v);
-      st_row8<BF>(sm + P::A1, tid, 2 * c + 1, kH, v + 8);
+      for (int j = 0; j < 4; ++j) st_row8_relu<BF>(sm + P::A1, tid, 4 * c + j, kH, v + 8 * j);
     }
     tc::fence_before_sync();
     tc::fence_async_smem();

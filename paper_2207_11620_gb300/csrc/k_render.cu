@@ -217,6 +217,11 @@ __global__ void k_raygen(nv_camera cam, int row0, int rows, float *ray, int *nex
   }
 }
 
+// Threads per CTA of k_coords (32, 64 and 128 measured alike on the 1080p
+// frame, although rays take different numbers of march steps and a CTA holds
+// its SM slot until its slowest warp ends).
+constexpr int kCoordsThreads = 128;
+
 // Next K sample positions of each live ray (A-12, march_step).
 // seg_exp (non-NULL: adaptive step between step and step_max): the opacity
 // exponent of each emitted sample; next_k then holds the ray parameter t.
@@ -224,7 +229,7 @@ __global__ void k_raygen(nv_camera cam, int row0, int rows, float *ray, int *nex
 // staged in shared memory ([thread][3K + 1] floats) and each warp writes its 32
 // rays' block with coalesced stores: one store per sample from every thread hit
 // a different sector per lane and kept the load/store queue full.
-__global__ void __launch_bounds__(128) k_coords(const float *__restrict__ ray, int *next_k, int64_t cap,
+__global__ void __launch_bounds__(kCoordsThreads) k_coords(const float *__restrict__ ray, int *next_k, int64_t cap,
                                                 const int *count, int K, float step, float step_max,
                                                 float alpha_exp, McView mc, float *coords, float *seg_exp,
                                                 int *nvalid) {
@@ -301,7 +306,7 @@ nv_status coords_kernel_setup() {
   static int done = 0;
   if (done) return NV_OK;
   cudaError_t e = cudaFuncSetAttribute(k_coords, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)((size_t)128 * (3 * 64 + 1) * sizeof(float)));
+                                       (int)((size_t)kCoordsThreads * (3 * 64 + 1) * sizeof(float)));
   if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(k_coords)");
   done = 1;
   return NV_OK;
@@ -472,8 +477,8 @@ __global__ void k_scale_double(double *x, double s) { *x *= s; }
 
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
 
-// Dynamic shared memory of k_coords: 128 threads x (3K + 1) floats.
-inline size_t coords_smem(int K) { return (size_t)128 * (3 * K + 1) * sizeof(float); }
+// Dynamic shared memory of k_coords: kCoordsThreads x (3K + 1) floats.
+inline size_t coords_smem(int K) { return (size_t)kCoordsThreads * (3 * K + 1) * sizeof(float); }
 
 }  // namespace
 
@@ -578,9 +583,9 @@ nv_status render_impl(nv_renderer *r, nv_ctx *net, const nv_volume *raw, const n
   while (bound > 0 && issued < max_iter) {
     const int nxt = cur ^ 1;
     int tk = net ? prof_begin(net) : -1;
-    k_coords<<<blocks_for(bound, 128), 128, coords_smem(K), st>>>(r->ray[cur], r->next_k[cur], cap, &r->counters[cur], K,
-                                                     o.step, o.step_max, o.alpha_exp, mv, r->coords, seg_exp,
-                                                     r->nvalid);
+    k_coords<<<blocks_for(bound, kCoordsThreads), kCoordsThreads, coords_smem(K), st>>>(
+        r->ray[cur], r->next_k[cur], cap, &r->counters[cur], K, o.step, o.step_max, o.alpha_exp, mv, r->coords,
+        seg_exp, r->nvalid);
     if (net) prof_end(net, NV_K_OTHER, tk);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_coords launch")) != NV_OK) break;
     if (net) {
@@ -671,8 +676,9 @@ nv_status render_raw_sync_loop(const nv_renderer &r, const nv_volume &raw, const
     if (it >= max_iter) return nv_fail(NV_ERR_STATE, "ray march did not finish within %lld iterations", (long long)max_iter);
     const int nxt = cur ^ 1;
     const int64_t bound = live;
-    k_coords<<<blocks_for(bound, 128), 128, coords_smem(K), st>>>(r.ray[cur], r.next_k[cur], cap, &r.counters[cur], K, o.step,
-                                                     0.f, o.alpha_exp, mv, r.coords, nullptr, r.nvalid);
+    k_coords<<<blocks_for(bound, kCoordsThreads), kCoordsThreads, coords_smem(K), st>>>(
+        r.ray[cur], r.next_k[cur], cap, &r.counters[cur], K, o.step, 0.f, o.alpha_exp, mv, r.coords, nullptr,
+        r.nvalid);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_coords launch")) != NV_OK) return s;
     k_values_raw<<<blocks_for(bound * K, 256), 256, 0, st>>>(raw, r.coords, &r.counters[cur], K, r.values);
     if ((s = nv_cuda_check(cudaGetLastError(), "k_values_raw launch")) != NV_OK) return s;

@@ -13,8 +13,12 @@
 //                    and the per-point input gradient dF, which each thread
 //                    scatters straight into the FP32 table gradient (A-7)
 //
-// The two run on chunks of at most kChunk points so the features of a chunk
-// (16 MB at D0 = 32) stay in L2 between the kernels.  The scatter's vector
+// The two run on chunks of points.  Passes that scatter gradients take at
+// most kChunk = 2^19 points (16 MB of features at D0 = 32, L2-resident
+// between the kernels).  Inference takes up to kChunkInfer = 2^23 (512 MB):
+// a render iteration's samples then go through in one or two launches, and
+// the ramp and tail every launch of either kernel pays cost more, at
+// 2^19-point chunks, than the features' round trip through HBM.  The scatter's vector
 // reductions keep the load/store path busy while the CTA's other phases wait
 // on the tensor core, so the MLP and the scatter overlap inside one kernel.
 //
@@ -42,6 +46,7 @@ constexpr int kH = 64;            // hidden width
 constexpr int kTP = 128;          // points per tile
 constexpr int kThreads = 256;     // two threads per point
 constexpr int64_t kChunk = 1 << 19;
+constexpr int64_t kChunkInfer = 1 << 23;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 // Descriptor field order of an MN-major no-swizzle operand: the leading byte
@@ -327,13 +332,13 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 
 #pragma unroll
       for (int c = 0; c < HH / 16; ++c) tc::tmem_ld16(tD1 + lane_base + hh * HH + c * 16, v + c * 16);
       tc::tmem_ld_wait();
+      if constexpr (kBwd) {
 #pragma unroll
-      for (int i = 0; i < HH; ++i) {
-        if (v[i] > 0.f) m1 |= 1u << i;
-        v[i] = fmaxf(v[i], 0.f);
+        for (int i = 0; i < HH; ++i)
+          if (v[i] > 0.f) m1 |= 1u << i;
       }
 #pragma unroll
-      for (int c = 0; c < HH / 8; ++c) st_row8<BF>(sm + P::A1, r, hh * (HH / 8) + c, kH, v + c * 8);
+      for (int c = 0; c < HH / 8; ++c) st_row8_relu<BF>(sm + P::A1, r, hh * (HH / 8) + c, kH, v + c * 8);
     }
     tc::fence_before_sync();
     tc::fence_async_smem();
@@ -651,9 +656,10 @@ bool tc_supported(const NetDesc &nd) {
 }
 
 // Scratch of the tensor-core path: one chunk of features (16-bit, tile layout)
-// and of sampled training points and targets (FP32), allocated on first use.
-static nv_status tc_scratch(nv_ctx *c, int64_t points) {
-  const int64_t cap = points < kChunk ? ((points + kTP - 1) / kTP) * kTP : kChunk;
+// and of sampled training points and targets (FP32), allocated on first use;
+// chunks of at most `chunk` points.
+static nv_status tc_scratch(nv_ctx *c, int64_t points, int64_t chunk) {
+  const int64_t cap = points < chunk ? ((points + kTP - 1) / kTP) * kTP : chunk;
   if (c->tc_cap >= cap) return NV_OK;
   cudaFree(c->tc_feat);
   cudaFree(c->tc_tgt);
@@ -676,8 +682,10 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
   nv_ctx *c = const_cast<nv_ctx *>(cc);
   if (!tc_supported(c->nd)) return nv_fail(NV_ERR_UNSUPPORTED, "tensor-core MLP: unsupported network shape");
   if (n_upper <= 0) return NV_OK;
-  nv_status s = tc_scratch(c, n_upper);
+  const int64_t chunk_max = (mode == MODE_INFER || mode == 3) ? kChunkInfer : kChunk;
+  nv_status s = tc_scratch(c, n_upper, chunk_max);
   if (s != NV_OK) return s;
+  const int64_t chunk = c->tc_cap < chunk_max ? c->tc_cap : chunk_max;
   PointSrc ps{};
   if (mode == 3) {
     ps.kind = 1;
@@ -701,8 +709,8 @@ nv_status launch_mlp_tc_ext(const nv_ctx *cc, int mode, const MlpArgs &a, const 
   // given points of a pass that scatters table gradients: the gather kernel
   // flags any outside [0,1]^3 (sampled ones never are)
   int *off_flag = (mode == MODE_TRAIN || mode == MODE_BACKWARD) && ps.kind == 0 ? &c->ds->off_domain : nullptr;
-  for (int64_t off = 0; off < n_upper; off += c->tc_cap) {
-    ChunkSpan cs{n_dev, n_mult, a.n, off, n_upper - off < c->tc_cap ? n_upper - off : c->tc_cap};
+  for (int64_t off = 0; off < n_upper; off += chunk) {
+    ChunkSpan cs{n_dev, n_mult, a.n, off, n_upper - off < chunk ? n_upper - off : chunk};
     int tk = prof_begin(c);
     s = launch_encode_tiles(c, ps, cs, c->tc_feat, tgt, xyz_out, off_flag, a.coherent != 0 || mode == 3,
                             c->stream);

@@ -48,16 +48,18 @@ __device__ __forceinline__ int march_step(const float *o, const float *d, float 
   const int cy = min(max((int)floorf(__fmul_rn(pos[1], mc.sy)), 0), mc.ncy - 1);
   const int cz = min(max((int)floorf(__fmul_rn(pos[2], mc.sz)), 0), mc.ncz - 1);
   if (__ldg(mc.mu + ((int64_t)cz * mc.ncy + cy) * mc.ncx + cx) != 0.0f) return kMarchSample;
-  // exit distance of this cell along the ray (approximate; only used to jump)
+  // exit distance of this cell along the ray, approximate (fast divisions: a
+  // few units in the last place, far inside the two-sample margin below); it
+  // only decides how far to jump, never which samples are taken
   const int cc[3] = {cx, cy, cz};
   const float sc[3] = {mc.sx, mc.sy, mc.sz};
   float texit = __int_as_float(0x7f800000);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (d[a] > 0.f) texit = fminf(texit, ((float)(cc[a] + 1) / sc[a] - o[a]) / d[a]);
-    else if (d[a] < 0.f) texit = fminf(texit, ((float)cc[a] / sc[a] - o[a]) / d[a]);
+    if (d[a] > 0.f) texit = fminf(texit, __fdividef(__fdividef((float)(cc[a] + 1), sc[a]) - o[a], d[a]));
+    else if (d[a] < 0.f) texit = fminf(texit, __fdividef(__fdividef((float)cc[a], sc[a]) - o[a], d[a]));
   }
-  const float kf = ceilf((texit - t0) / step - 0.5f) - 2.0f;
+  const float kf = ceilf(__fdividef(texit - t0, step) - 0.5f) - 2.0f;
   int kj = k + 1;
   if (kf > (float)kj) kj = (kf < 2.0e9f) ? (int)kf : 2000000000;
   k = kj;

@@ -99,6 +99,28 @@ __device__ __forceinline__ void st_row8(uint8_t *base, int r, int c, int K, cons
   *reinterpret_cast<uint4 *>(base + tile_off(r, c * 8, K)) = u;
 }
 
+// max(a, 0) and max(b, 0) rounded to 16 bits and packed (a in the low half):
+// one conversion with the ReLU built in.  Rounding commutes with the clamp, so
+// this equals pack16x2(fmaxf(a, 0), fmaxf(b, 0)) but for the sign of a zero.
+template <bool BF>
+__device__ __forceinline__ uint32_t pack16x2_relu(float a, float b) {
+  uint32_t r;
+  if constexpr (BF) asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  else asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+
+// st_row8 of max(v, 0).
+template <bool BF>
+__device__ __forceinline__ void st_row8_relu(uint8_t *base, int r, int c, int K, const float *v) {
+  uint4 u;
+  u.x = pack16x2_relu<BF>(v[0], v[1]);
+  u.y = pack16x2_relu<BF>(v[2], v[3]);
+  u.z = pack16x2_relu<BF>(v[4], v[5]);
+  u.w = pack16x2_relu<BF>(v[6], v[7]);
+  *reinterpret_cast<uint4 *>(base + tile_off(r, c * 8, K)) = u;
+}
+
 // Shared-memory descriptor of a K-major [rows][K] no-swizzle operand: the next
 // 8 K values are 128 B on, the next 8 rows K * 16 B on.
 __device__ __forceinline__ uint64_t desc_k(uint32_t saddr, int K) {
@@ -151,7 +173,7 @@ __device__ __forceinline__ void row_weights(int q, float wx, float wy, float wz,
   w1 = __fmul_rn(wx, wyz);
 }
 __device__ __forceinline__ float blend2(float acc, float w0, float v0, float w1, float v1) {
-  return __fadd_rn(acc, __fmaf_rn(w0, v0, __fmul_rn(w1, v1)));
+  return __fmaf_rn(w1, v1, __fmaf_rn(w0, v0, acc));
 }
 
 // A-1..A-3 for G consecutive levels, x-paired: corners (cx, .) and (cx + 1, .)

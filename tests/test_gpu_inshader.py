@@ -53,6 +53,28 @@ def test_inshader_equals_streaming_ortho(nv, prec, shape):
     assert 0 < sam.item() <= 70 * 37 * 128
 
 
+def test_streaming_over_several_inference_chunks_equals_inshader(nv):
+    """A 1280 x 1024 orthographic frame over the unit square: 1.3 M rays,
+    10.5 M samples in the first streaming iteration at K = 8, which the
+    tensor-core path takes in two inference chunks (2^23 points each at most);
+    the in-shader kernel evaluates the same samples without chunks."""
+    c = CF.CFG2_NET
+    net = nv.NeuralVolume(prec="fp16", **c.kwargs())
+    net.set_params(varied_params(net, c, 52))
+    W, H = 1280, 1024
+    cam = I.ortho_camera_z(W, H)
+    lut = torch.from_numpy(I.ramp_lut()).cuda()
+    opts = dict(step=1 / 128, alpha_exp=1.0, et=0.99, K=8)
+    r = nv.Renderer(W * H, K=8)
+    ss = r.render(cam, lut, opts, net=net)
+    it, ns = r.stats()
+    is_ = nv.render_inshader(net, cam, lut, opts)
+    torch.cuda.synchronize()
+    assert ns >= W * H * 8 > (1 << 23)  # the first iteration alone: 8 samples of every ray
+    d = (is_ - ss).abs().max().item()
+    assert d <= 1e-6, d
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_inshader_perspective_macrocells_matches_streaming_and_oracle(nv, prec):
     c = CF.CFG2_NET
