@@ -678,28 +678,32 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
 def gather_roofline(ns, g_ms, L, F, D0, pk, pk_kind, l2pk):
     """Roofline of the render gather (k_encode_tiles in inference) over one frame of ns
     decoded samples: 8 corners x L levels x F 16-bit features per sample (512 B at L16
-    F2), 5 (F = 2) or 6 (F = 4) 16-byte loads issued per level.  The K samples of a
-    ray sit in adjacent lanes and share most corners, so these loads resolve in L1:
-    the bound is the measured rate of scattered 16-byte loads from an L1-resident
-    buffer (x 16 B); the same bytes are also set against the L2-resident scattered
-    load rate and, with the coordinates read (12 B) and the feature row written
-    (2 D0 B), against HBM."""
+    F2), each corner one load of its 2F-byte entry (8 loads per level).  The K samples
+    of a ray sit in adjacent lanes and neighbouring rays share most corners, so these
+    loads resolve in L1: the bytes are set against the measured rate of scattered
+    16-byte loads from an L1-resident buffer (x 16 B) and from an L2-resident one.
+    Lanes that share an address share a sector, so the issued loads can exceed the
+    scattered-load rate; what bounds the kernel is instruction issue (ncu: 2.8 of 4
+    instructions per SM cycle, no pipe above 40%).  Its own HBM traffic is the
+    coordinates read (12 B) and the feature row written (2 D0 B) per sample."""
     g_bytes = ns * 8 * L * F * 2
     g_ach = g_bytes / (g_ms / 1e3) / 1e9
-    loads = ns * L * (5 if F == 2 else 6)
+    loads = ns * L * 8
     l1 = l2pk["l1_gather_loads_per_s"]
-    hbm = ns * (8 * L * F * 2 + 12 + 2 * D0) / (g_ms / 1e3) / 1e9
+    hbm = ns * (12 + 2 * D0) / (g_ms / 1e3) / 1e9
     return {"kernel": "k_encode_tiles", "bound": "l1", "achieved": g_ach, "peak": l1 * 16 / 1e9, "unit": "GB/s",
             "frac": g_ach / (l1 * 16 / 1e9),
             "peak_kind": "measured: scattered 16-byte loads from an L1-resident 32 KiB (nv_peak_gather) x 16 B",
             "algorithmic_bytes_per_frame": g_bytes, "ms_per_frame": g_ms,
-            "issued_16B_loads": {"per_frame": loads, "achieved_per_s": loads / (g_ms / 1e3), "peak_per_s": l1,
-                                 "frac": loads / (g_ms / 1e3) / l1},
+            "limiter": "instruction issue (ncu: 2.8 of 4 per SM cycle, ALU / FMA / LSU pipes 36 / 39 / 19%); "
+                       "profiles/k_encode_tiles_render1080p.md",
+            "issued_corner_loads": {"per_frame": loads, "bytes_each": 2 * F, "achieved_per_s": loads / (g_ms / 1e3),
+                                    "scattered_16B_load_peak_per_s": l1, "frac": loads / (g_ms / 1e3) / l1},
             "l2": {"achieved": g_ach, "peak": l2pk["gather_loads_per_s"] * 16 / 1e9, "unit": "GB/s",
                    "frac": g_ach / (l2pk["gather_loads_per_s"] * 16 / 1e9),
                    "peak_kind": "measured: scattered 16-byte loads from 32 MiB (nv_peak_gather) x 16 B"},
             "hbm": {"achieved": hbm, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm / pk["hbm_gbs"],
-                    "peak_kind": pk_kind + " (copy)"}}
+                    "peak_kind": pk_kind + " (copy)", "bytes_per_sample": 12 + 2 * D0}}
 
 
 def oracle_render_rate(net, params, cam, lut, opts, mu, shape, stride=10):
