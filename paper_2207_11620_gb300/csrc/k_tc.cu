@@ -257,14 +257,21 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t tD1 = tmem + P::kColD1, tD2 = tmem + P::kColD2;
 
-  // feature copies issued (by thread 0) into each buffer, and which are not yet waited for
-  uint32_t uses[2] = {0, 0};
-  bool pend[2] = {false, false};
+  // feature copies issued (by thread 0) into each buffer, and which are not yet
+  // waited for (scalars rather than arrays indexed by the buffer, which would
+  // live in local memory on the MMA-issuing thread's path)
+  uint32_t uses0 = 0, uses1 = 0;
+  bool pend0 = false, pend1 = false;
   auto issue_tile = [&](int b, int64_t t) {
     tc::mbar_expect_tx(lbar + b, P::kTile);
     tc::bulk_g2s(sm + P::A0 + b * P::kTile, feat + t * P::kTile, P::kTile, lbar + b);
-    ++uses[b];
-    pend[b] = true;
+    if (b) {
+      ++uses1;
+      pend1 = true;
+    } else {
+      ++uses0;
+      pend0 = true;
+    }
   };
   // first feature tile of this CTA
   if (tid == 0 && (int64_t)blockIdx.x < ntiles) issue_tile(0, blockIdx.x);
@@ -314,7 +321,8 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 
     const bool ok_ld = tc::mbar_wait(lbar + buf, (uint32_t)(it >> 1) & 1u, kWaitLimit);
     if (__syncthreads_or(!ok_ld)) { failed = true; break; }
     if (tid == 0) {
-      pend[buf] = false;
+      if (buf) pend1 = false;
+      else pend0 = false;
       const int64_t nt = tile + gridDim.x;
       if (nt < ntiles) issue_tile(buf ^ 1, nt);
       // ---- layer 0: D1 = A0 W0^T ----
@@ -567,8 +575,8 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 
   if (tid == 0) {
     // a feature copy still in flight (only after an early exit) must land
     // before the CTA's shared memory is released
-    for (int b = 0; b < 2; ++b)
-      if (pend[b]) tc::mbar_wait(lbar + b, (uses[b] - 1) & 1u, kWaitLimit);
+    if (pend0) tc::mbar_wait(lbar, (uses0 - 1) & 1u, kWaitLimit);
+    if (pend1) tc::mbar_wait(lbar + 1, (uses1 - 1) & 1u, kWaitLimit);
   }
   if (failed) {
     // give an MMA that may still be in flight one more bounded chance to finish
