@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kH = 64;    // hidden width
 constexpr int kTP = 128;  // rays (threads) per CTA = tile rows
+constexpr int kIsTW = 16;  // a CTA's rays: a kIsTW x (kTP / kIsTW) pixel tile
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint32_t kTmemCols = 128;  // D1 (64) + D2 (64)
 
@@ -87,18 +88,22 @@ __global__ void __launch_bounds__(kTP) k_render_is(NetDesc nd, const float *__re
   const uint32_t tD1 = tmem, tD2 = tmem + 64;
   const uint32_t id_fwd = tc::idesc_f16(128, kH, BF, false, false);
 
-  // ---- this thread's ray (A-11) ----
-  const int64_t npix = (int64_t)cam.width * cam.height;
-  const int64_t pix = (int64_t)blockIdx.x * kTP + tid;
+  // ---- this thread's ray (A-11): a CTA takes a 16 x 8 pixel tile, so its
+  // rays' samples share table lines at the mid levels ----
+  const int tiles_x = (cam.width + kIsTW - 1) / kIsTW;
+  const int px = (int)(blockIdx.x % tiles_x) * kIsTW + tid % kIsTW;
+  const int py = (int)(blockIdx.x / tiles_x) * (kTP / kIsTW) + tid / kIsTW;
+  const int64_t pix = (int64_t)py * cam.width + px;
   float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f}, t0 = 0.f, t1 = 0.f;
   bool live = false;
-  if (pix < npix) {
-    nv_camera_ray(cam, (int)(pix % cam.width), (int)(pix / cam.width), o, d);
+  if (px < cam.width && py < cam.height) {
+    nv_camera_ray(cam, px, py, o, d);
     live = nv_box(o, d, t0, t1);
     if (!live) rgba[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   float cr = 0.f, cg = 0.f, cb = 0.f, ca = 0.f;
   int k = 0;
+  McCache cache;
   unsigned nsamp = 0;
   uint32_t phase = 0;
   bool failed = false;
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(kTP) k_render_is(NetDesc nd, const float *__re
     float pos[3] = {0.f, 0.f, 0.f};
     if (live) {
       int m;
-      while ((m = march_step(o, d, t0, t1, step, mc, k, pos)) == kMarchSkip) {
+      while ((m = march_step(o, d, t0, t1, step, mc, k, pos, &cache)) == kMarchSkip) {
       }
       if (m == kMarchEnd) {
         live = false;  // left the volume
@@ -232,8 +237,8 @@ nv_status launch_is(nv_ctx *c, const nv_camera &cam, const float *lut, const McV
   if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(k_render_is)");
   e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(carveout)");
-  const int64_t npix = (int64_t)cam.width * cam.height;
-  const unsigned grid = (unsigned)((npix + kTP - 1) / kTP);
+  const int64_t tiles_x = (cam.width + kIsTW - 1) / kIsTW, tiles_y = (cam.height + kTP / kIsTW - 1) / (kTP / kIsTW);
+  const unsigned grid = (unsigned)(tiles_x * tiles_y);
   kern<<<grid, kTP, bytes, c->stream>>>(c->nd, c->params, reinterpret_cast<const uint16_t *>(c->shadow), cam, mv,
                                         lut, o.step, o.alpha_exp, o.et, reinterpret_cast<float4 *>(rgba), samples,
                                         &c->ds->err);

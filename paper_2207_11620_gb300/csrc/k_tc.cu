@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_fold_replicas(const __grid_constant__ N
 // TRAIN / BACKWARD add the weight gradients and the table gradient w_corner * dF
 // into a.grads.  tgt_buf: the targets of a sampled training batch, [chunk rows].
 template <int D0, bool BF, int MODE>
-__global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 3 : 2) k_mlp_tc(NetDesc nd, const float *__restrict__ params,
+__global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 4 : 2) k_mlp_tc(NetDesc nd, const float *__restrict__ params,
                                                         const uint16_t *__restrict__ shadow, MlpArgs a,
                                                         PointSrc ps, ChunkSpan cs,
                                                         const uint8_t *__restrict__ feat,

@@ -37,8 +37,27 @@ inline McView mc_view(const nv_macrocells *mc) {
 // that skip and the lanes that take samples advance together.
 enum { kMarchEnd = 0, kMarchSample = 1, kMarchSkip = 2 };
 
+// McCache: the last macrocell a ray looked up and its mu_max (idx -1: none), so
+// the run of samples inside one cell loads its value once.  The in-shader
+// kernel keeps it across its iterations; the streaming march's walk (whose
+// lookups hit L1) measured 2-4% slower with it and passes none.
+struct McCache {
+  int idx = -1;
+  float mu = 0.f;
+};
+
+__device__ __forceinline__ float mc_lookup(const McView &mc, int cx, int cy, int cz, McCache *cache) {
+  const int ci = (cz * mc.ncy + cy) * mc.ncx + cx;
+  if (!cache) return __ldg(mc.mu + ci);
+  if (ci != cache->idx) {
+    cache->idx = ci;
+    cache->mu = __ldg(mc.mu + ci);
+  }
+  return cache->mu;
+}
+
 __device__ __forceinline__ int march_step(const float *o, const float *d, float t0, float t1, float step,
-                                          const McView &mc, int &k, float *pos) {
+                                          const McView &mc, int &k, float *pos, McCache *cache = nullptr) {
   const float tk = __fadd_rn(t0, __fmul_rn(__fadd_rn((float)k, 0.5f), step));
   if (!(tk < t1)) return kMarchEnd;
 #pragma unroll
@@ -47,7 +66,7 @@ __device__ __forceinline__ int march_step(const float *o, const float *d, float 
   const int cx = min(max((int)floorf(__fmul_rn(pos[0], mc.sx)), 0), mc.ncx - 1);
   const int cy = min(max((int)floorf(__fmul_rn(pos[1], mc.sy)), 0), mc.ncy - 1);
   const int cz = min(max((int)floorf(__fmul_rn(pos[2], mc.sz)), 0), mc.ncz - 1);
-  if (__ldg(mc.mu + ((int64_t)cz * mc.ncy + cy) * mc.ncx + cx) != 0.0f) return kMarchSample;
+  if (mc_lookup(mc, cx, cy, cz, cache) != 0.0f) return kMarchSample;
   // exit distance of this cell along the ray, approximate (fast divisions: a
   // few units in the last place, far inside the two-sample margin below); it
   // only decides how far to jump, never which samples are taken
