@@ -753,6 +753,14 @@ def bench_render_1080p(nv, I, CF, torch, frames, pk, pk_kind, l2pk, cpu=True):
     img, ms = _time_render(r, torch, frames, cam=cam, lut=lut, opts=opts, net=net, mc=mc)
     it, ns = r.stats()
     psnr = _psnr(nv.image_mse(img, raw).item())
+    # the same frame by in-shader inference (Sec. 5.1, App. A): one megakernel
+    sam = torch.zeros(1, dtype=torch.int64, device="cuda")
+    is_img = torch.empty_like(img)
+    is_img, is_ms = _median_frame_ms(
+        torch, frames, lambda: nv.render_inshader(net, cam, lut, opts, mc=mc, out=is_img, samples=sam))
+    inshader = {"frame_ms": is_ms, "samples_per_frame": int(sam.item()),
+                "decoded_samples_per_s": int(sam.item()) / (is_ms / 1e3),
+                "max_abs_diff_vs_streaming": float((is_img - img).abs().max().item())}
     # per-kernel device times over the same frames, read after every frame (the
     # library keeps at most 8192 timed launches between reads; a frame has ~800)
     net.profile(True)
@@ -782,6 +790,8 @@ def bench_render_1080p(nv, I, CF, torch, frames, pk, pk_kind, l2pk, cpu=True):
                        "perspective, step 0.5 voxel, 16^3 macrocells, ET 0.99, K 8",
            "frame_ms": ms, "frames": frames, "iterations": it, "samples_per_frame": ns,
            "decoded_samples_per_s": ns / (ms / 1e3), "image_psnr_db_vs_raw": psnr,
+           "path": "sample streaming (nv_render); the same image in-shader (nv_render_inshader) below",
+           "inshader": inshader,
            "raw_volume_frame_ms": raw_ms, "raw_iterations": raw_it, "raw_samples_per_frame": raw_ns,
            "kernels_ms_per_frame": per, "launches_per_frame": launches,
            "roofline": roof,

@@ -28,7 +28,10 @@ constexpr int kH = 64;    // hidden width
 constexpr int kTP = 128;  // rays (threads) per CTA = tile rows
 constexpr int kIsTW = 16;  // a CTA's rays: a kIsTW x (kTP / kIsTW) pixel tile
 constexpr uint32_t kWaitLimit = 1u << 24;
-constexpr uint32_t kTmemCols = 128;  // D1 (64) + D2 (64)
+// D1 and D2 share 64 columns: layer 1's product is issued only after every
+// thread's loads of D1 have completed, so a CTA needs 64 columns and up to six
+// CTAs (registers and shared memory allow six) share an SM.
+constexpr uint32_t kTmemCols = 64;
 
 template <int D0>
 struct IsPlan {
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(kTP) k_render_is(NetDesc nd, const float *__re
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  const uint32_t tD1 = tmem, tD2 = tmem + 64;
+  const uint32_t tD1 = tmem, tD2 = tmem;
   const uint32_t id_fwd = tc::idesc_f16(128, kH, BF, false, false);
 
   // ---- this thread's ray (A-11): a CTA takes a 16 x 8 pixel tile, so its
@@ -227,7 +230,7 @@ nv_status launch_is(nv_ctx *c, const nv_camera &cam, const float *lut, const McV
                     float *rgba, unsigned long long *samples) {
   using P = IsPlan<D0>;
   // tensor memory holds 512 columns per SM: size the shared-memory request so
-  // that at most 512 / 128 = 4 CTAs share an SM
+  // that at most 512 / kTmemCols CTAs share an SM
   const int tmem_cap = 512 / (int)kTmemCols;
   size_t bytes = P::TOTAL + 1024;
   const size_t min_bytes = 233472 / (tmem_cap + 1) + 1024;
