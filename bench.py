@@ -818,7 +818,9 @@ def bench_render_1080p(nv, I, CF, torch, frames, pk, pk_kind, l2pk, cpu=True):
 def extra_cfg4_inloop(nv, I, CF, torch, pk, pk_kind, l2pk, frames=None):
     """Config 4: 1024^3 volume in HBM; each frame one 2^18-point training step and a
     1024x1024 render of the current FP16 network; ms/frame and the PSNR of the
-    last frame against the raw-volume render."""
+    last frame against the raw-volume render.  The loop runs twice on fresh
+    networks: rendering by sample streaming (the reported figures) and by the
+    in-shader megakernel (inshader_loop)."""
     cfg = CF.CFG4
     c = cfg["net"]
     D = cfg["volume"]
@@ -831,35 +833,49 @@ def extra_cfg4_inloop(nv, I, CF, torch, pk, pk_kind, l2pk, frames=None):
     r = nv.Renderer(W * H, K=cfg["K"])
     raw, raw_ms = _time_render(r, torch, 2, cam=cam, lut=lut, opts=opts, raw=vt, mc=mc)
     raw = raw.clone()
-    net = nv.NeuralVolume(prec="fp16", **c.kwargs())
-    net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
-    psnr_curve = []
-    # online macrocells (Sec. 5.3): the training samples grow the value ranges,
-    # mu_max is refreshed from them before each frame's render
     cell = cfg["cell"]
-    mm_on = nv.online_macrocells(vt.shape, cell)
-    mu_on = torch.zeros_like(mu)
-    net.set_online_macrocells(mm_on, vt.shape, cell)
-    mc_on = (mu_on, cell, vt.shape)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    split = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(frames)]
-    e0.record()
-    for f in range(frames):
-        split[f][0].record()
-        net.train_step(n=cfg["batch"], vol=vt, seed=21, loss_out=loss)
-        nv.macrocells_mu(mm_on, vt.shape, cell, lut, out=mu_on)
-        split[f][1].record()
-        r.render(cam, lut, opts, net=net, mc=mc_on, out=img)
-        split[f][2].record()
-        if f % 100 == 99:
-            psnr_curve.append((f + 1, nv.image_mse(img, raw)))
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / frames
-    train_ms = statistics.median(a.elapsed_time(b) for a, b, _ in split)
-    render_ms = statistics.median(b.elapsed_time(c2) for _, b, c2 in split)
+
+    def in_loop(render):
+        """frames x (one training step, mu_max from the online ranges, one render) of a
+        fresh network; returns the network, its online macrocells and the timings."""
+        net = nv.NeuralVolume(prec="fp16", **c.kwargs())
+        net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
+        psnr_curve = []
+        # online macrocells (Sec. 5.3): the training samples grow the value ranges,
+        # mu_max is refreshed from them before each frame's render
+        mm_on = nv.online_macrocells(vt.shape, cell)
+        mu_on = torch.zeros_like(mu)
+        net.set_online_macrocells(mm_on, vt.shape, cell)
+        mc_on = (mu_on, cell, vt.shape)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        split = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(frames)]
+        e0.record()
+        for f in range(frames):
+            split[f][0].record()
+            net.train_step(n=cfg["batch"], vol=vt, seed=21, loss_out=loss)
+            nv.macrocells_mu(mm_on, vt.shape, cell, lut, out=mu_on)
+            split[f][1].record()
+            render(net, mc_on)
+            split[f][2].record()
+            if f % 100 == 99:
+                psnr_curve.append((f + 1, nv.image_mse(img, raw)))
+        e1.record()
+        torch.cuda.synchronize()
+        t = {"ms_per_frame": e0.elapsed_time(e1) / frames,
+             "train_ms_per_frame": statistics.median(a.elapsed_time(b) for a, b, _ in split),
+             "render_ms_per_frame": statistics.median(b.elapsed_time(c2) for _, b, c2 in split),
+             "psnr_db_by_frame": [(f, _psnr(m.item())) for f, m in psnr_curve]}
+        t["final_psnr_db"] = t["psnr_db_by_frame"][-1][1] if psnr_curve else None
+        return net, mu_on, mc_on, t
+
+    # the same loop with the in-shader megakernel (Sec. 5.1) as the renderer
+    net, _, _, t_is = in_loop(lambda n, m: nv.render_inshader(n, cam, lut, opts, mc=m, out=img))
+    net.close()
+    net, mu_on, mc_on, t_ss = in_loop(lambda n, m: r.render(cam, lut, opts, net=n, mc=m, out=img))
+    ms, train_ms, render_ms = t_ss["ms_per_frame"], t_ss["train_ms_per_frame"], t_ss["render_ms_per_frame"]
+    curve = t_ss["psnr_db_by_frame"]
     # per-kernel times of the two halves, each profiled on its own over a few more frames
     net.profile(True)
     for k in ("encode", "mlp", "scatter", "adam", "other", "render"):
@@ -883,7 +899,6 @@ def extra_cfg4_inloop(nv, I, CF, torch, pk, pk_kind, l2pk, frames=None):
     train_roof = {k: roofline_of(k, avg, "fp16", pk, pk_kind, cfg["batch"], n_visit, net.n_table, c.dims, c.L,
                                  c.F, l2pk) for k in ("encode", "mlp", "adam") if k in avg}
     render_roof = gather_roofline(ns, kt_render["encode"][0] / nprof, c.L, c.F, c.dims[0], pk, pk_kind, l2pk)
-    curve = [(f, _psnr(m.item())) for f, m in psnr_curve]
     # the last network rendered with ranges precomputed from the voxels instead
     img_pre = r.render(cam, lut, opts, net=net, mc=mc)
     psnr_pre = _psnr(nv.image_mse(img_pre, raw).item())
@@ -897,7 +912,8 @@ def extra_cfg4_inloop(nv, I, CF, torch, pk, pk_kind, l2pk, frames=None):
            "raw_ms": raw_ms, "psnr_db_by_frame": curve,
            "final_psnr_db": curve[-1][1] if curve else None, "n_params": net.n_params,
            "macrocells": "online (training samples)", "final_psnr_db_precomputed_macrocells": psnr_pre,
-           "nonempty_cells_online": cells_on, "nonempty_cells_precomputed": cells_pre}
+           "nonempty_cells_online": cells_on, "nonempty_cells_precomputed": cells_pre,
+           "inshader_loop": t_is}
     net.close()
     r.close()
     del vt

@@ -29,8 +29,8 @@ constexpr int kTP = 128;  // rays (threads) per CTA = tile rows
 constexpr int kIsTW = 16;  // a CTA's rays: a kIsTW x (kTP / kIsTW) pixel tile
 constexpr uint32_t kWaitLimit = 1u << 24;
 // D1 and D2 share 64 columns: layer 1's product is issued only after every
-// thread's loads of D1 have completed, so a CTA needs 64 columns and up to six
-// CTAs (registers and shared memory allow six) share an SM.
+// thread's loads of D1 have completed, so a CTA needs 64 columns and seven CTAs
+// (72 registers, 31 KB of shared memory at L*F = 32) share an SM.
 constexpr uint32_t kTmemCols = 64;
 
 template <int D0>
@@ -38,14 +38,16 @@ struct IsPlan {
   static constexpr int W0 = 0;                  // B [64][D0]
   static constexpr int W1 = W0 + kH * D0 * 2;   // B [64][64]
   static constexpr int A0 = W1 + kH * kH * 2;   // A [128][D0] features of this iteration's samples
-  static constexpr int A1 = A0 + kTP * D0 * 2;  // A [128][64] h1
+  // A [128][64] h1, over the features: written after layer 0's product has
+  // read them, and the next features are written after layer 1's has read it
+  static constexpr int A1 = A0;
   static constexpr int W2 = A1 + kTP * kH * 2;  // float [64]
   static constexpr int BAR = W2 + kH * 4;       // mbarrier + tensor-memory slot
   static constexpr int TOTAL = BAR + 16;
 };
 
 template <int D0, int F, bool BF>
-__global__ void __launch_bounds__(kTP) k_render_is(NetDesc nd, const float *__restrict__ params,
+__global__ void __launch_bounds__(kTP, 7) k_render_is(NetDesc nd, const float *__restrict__ params,
                                                    const uint16_t *__restrict__ shadow, nv_camera cam, McView mc,
                                                    const float *__restrict__ lut, float step, float alpha_exp,
                                                    float et, float4 *__restrict__ rgba,
