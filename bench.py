@@ -1032,7 +1032,8 @@ def run_extras(args, pk, pk_kind, l2pk):
 def run_case(args):
     """Profiling cases (for ncu captures); each prints one JSON line.
 
-    train_cfg2    args.warmup + args.steps config-2 training steps (FP16, 2^18 sampled points)
+    train_cfg2    args.warmup + args.steps config-2 training steps (2^18 sampled points; FP16, or
+                  the precision --prec names)
     render1080p   the config-3 1080p frame of a trained FP16 network: 2000 training steps, one
                   frame, then args.steps frames (and the timing helper's first call) in the NVTX
                   range "frame"
@@ -1046,7 +1047,7 @@ def run_case(args):
     if args.case == "train_cfg2":
         cfg = CF.CFG2
         c = cfg["net"]
-        net = nv.NeuralVolume(prec="fp16", **c.kwargs())
+        net = nv.NeuralVolume(prec="fp16" if args.prec == "auto" else args.prec, **c.kwargs())
         net.set_params(I.init_params(net.n_table, net.n_params - net.n_table, seed=5, dims=c.dims))
         vol = torch.from_numpy(I.blob_volume(cfg["volume"], seed=cfg["volume_seed"])).cuda()
         loss = torch.zeros(1, dtype=torch.float64, device="cuda")
