@@ -228,12 +228,13 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 
         __ldg(reinterpret_cast<const uint4 *>(w1g + nn * kH + c * 8));
   }
   if constexpr (kBwd) {
+    // the transposes read consecutive elements of a weight row per warp (coalesced)
     for (int i = tid; i < kH * kH; i += kThreads) {  // W1^T: B[n][k] = W1[k][n]
-      const int nn = i / kH, k = i % kH;
+      const int nn = i % kH, k = i / kH;
       *reinterpret_cast<uint16_t *>(sm + P::W1T + tile_off(nn, k, kH)) = w1g[k * kH + nn];
     }
     for (int i = tid; i < D0 * kH; i += kThreads) {  // W0^T: B[n][k] = W0[k][n], n < D0, k < 64
-      const int nn = i / kH, k = i % kH;
+      const int nn = i % D0, k = i / D0;
       *reinterpret_cast<uint16_t *>(sm + P::W0T + tile_off(nn, k, kH)) = w0g[k * D0 + nn];
     }
   }
@@ -317,6 +318,11 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 
         tgt = a.in[p];
       }
     }
+    // the point itself, for the table scatter at the end of the tile: loaded now,
+    // so its round trip hides under the tile's products instead of delaying the
+    // scatter
+    float3 xs = make_float3(0.f, 0.f, 0.f);
+    if (kBwd && valid) xs = point_at(ps, p);
     // ---- this tile's features; start the next tile's copy into the other buffer ----
     const bool ok_ld = tc::mbar_wait(lbar + buf, (uint32_t)(it >> 1) & 1u, kWaitLimit);
     if (__syncthreads_or(!ok_ld)) { failed = true; break; }
@@ -498,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_INFER || MODE == 3) ? 
 #pragma unroll
           for (int i = 0; i < DH; i += 4) dst[i / 4] = make_float4(df[i], df[i + 1], df[i + 2], df[i + 3]);
         }
-        const float3 x = point_at(ps, p);
+        const float3 x = xs;
         // the coarsest levels (all in half 0) go to this CTA's dense replica
         const bool dense = hh == 0 && a.hot.levels > 0 && x.x >= 0.f && x.x <= 1.f && x.y >= 0.f && x.y <= 1.f &&
                            x.z >= 0.f && x.z <= 1.f;
