@@ -792,6 +792,7 @@ def bench_render_1080p(nv, I, CF, torch, frames, pk, pk_kind, l2pk, cpu=True):
            "decoded_samples_per_s": ns / (ms / 1e3), "image_psnr_db_vs_raw": psnr,
            "path": "sample streaming (nv_render); the same image in-shader (nv_render_inshader) below",
            "inshader": inshader,
+           "best_frame_ms": min(ms, is_ms), "best_path": "in-shader" if is_ms < ms else "sample streaming",
            "raw_volume_frame_ms": raw_ms, "raw_iterations": raw_it, "raw_samples_per_frame": raw_ns,
            "kernels_ms_per_frame": per, "launches_per_frame": launches,
            "roofline": roof,
