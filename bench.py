@@ -675,6 +675,10 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
     return out
 
 
+# warp instructions per sample and level of the render gather (ncu, trained 1080p frame)
+RENDER_GATHER_INSTR_PER_SAMPLE_LEVEL = 112
+
+
 def gather_roofline(ns, g_ms, L, F, D0, pk, pk_kind, l2pk):
     """Roofline of the render gather (k_encode_tiles in inference) over one frame of ns
     decoded samples: 8 corners x L levels x F 16-bit features per sample (512 B at L16
@@ -691,7 +695,7 @@ def gather_roofline(ns, g_ms, L, F, D0, pk, pk_kind, l2pk):
     loads = ns * L * 8
     l1 = l2pk["l1_gather_loads_per_s"]
     hbm = ns * (12 + 2 * D0) / (g_ms / 1e3) / 1e9
-    return {"kernel": "k_encode_tiles", "bound": "l1", "achieved": g_ach, "peak": l1 * 16 / 1e9, "unit": "GB/s",
+    out = {"kernel": "k_encode_tiles", "bound": "l1", "achieved": g_ach, "peak": l1 * 16 / 1e9, "unit": "GB/s",
             "frac": g_ach / (l1 * 16 / 1e9),
             "peak_kind": "measured: scattered 16-byte loads from an L1-resident 32 KiB (nv_peak_gather) x 16 B",
             "algorithmic_bytes_per_frame": g_bytes, "ms_per_frame": g_ms,
@@ -704,6 +708,23 @@ def gather_roofline(ns, g_ms, L, F, D0, pk, pk_kind, l2pk):
                    "peak_kind": "measured: scattered 16-byte loads from 32 MiB (nv_peak_gather) x 16 B"},
             "hbm": {"achieved": hbm, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm / pk["hbm_gbs"],
                     "peak_kind": pk_kind + " (copy)", "bytes_per_sample": 12 + 2 * D0}}
+    if F == 2 and D0 == 32:
+        # the bound itself: warp instructions issued against the SMs' issue rate (one per SM
+        # sub-partition and cycle at the maximum clock), with the instructions per sample and
+        # level of the committed ncu capture of this kernel on this workload
+        import torch
+        try:
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        except Exception:  # no device to ask: GB300's count
+            sms = 152
+        ipl = RENDER_GATHER_INSTR_PER_SAMPLE_LEVEL
+        achieved = ipl * ns * L / 32 / (g_ms / 1e3)
+        peak = 4 * sms * pk.get("sm_max_mhz", 2070.0) * 1e6
+        out["issue"] = {"warp_instructions_per_sample_and_level": ipl, "achieved_per_s": achieved,
+                        "peak_per_s": peak, "frac": achieved / peak,
+                        "source": "ncu sm__inst_executed of k_encode_tiles on this frame, "
+                                  "profiles/k_encode_tiles_render1080p.md"}
+    return out
 
 
 def oracle_render_rate(net, params, cam, lut, opts, mu, shape, stride=10):
