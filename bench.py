@@ -625,6 +625,11 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
         sh_img, sh_ms = _time_render(r, torch, frames, cam=cam, lut=lut,
                                      opts=dict(opts, shade=1, light=light, ambient=0.25), net=net, mc=mc)
         sh_it, sh_ns = r.stats()
+        # the same shadows by the in-shader megakernel
+        is_sh = torch.empty_like(sh_img)
+        is_sh, is_sh_ms = _median_frame_ms(
+            torch, frames, lambda: nv.render_inshader(net, cam, lut, dict(opts, shade=1, light=light, ambient=0.25),
+                                                      mc=mc, out=is_sh))
         pt_opts = dict(density=float(D), light=light, max_bounces=8, seed=3)
         _, pt_ms = _median_frame_ms(torch, frames, lambda: r.render_pt(cam, lut, pt_opts, mc, net=net))
         pt_it, pt_ns = r.stats()
@@ -639,7 +644,9 @@ def extra_cfg3_render(nv, I, CF, torch, train_steps=None, frames=9):
                                   "streaming_speedup": is_ms / ms},
                      "adaptive_step": {"step_max_voxels": cfg["step_voxels"] * 2 * cfg["cell"], "frame_ms": ad_ms,
                                        "samples_per_frame": ad_ns, "iterations": ad_it, "image_psnr_db": ad_psnr},
-                     "single_shot_shadows": {"frame_ms": sh_ms, "samples_per_frame": sh_ns, "iterations": sh_it},
+                     "single_shot_shadows": {"frame_ms": sh_ms, "samples_per_frame": sh_ns, "iterations": sh_it,
+                                             "inshader_frame_ms": is_sh_ms,
+                                             "inshader_max_abs_diff": float((is_sh - sh_img).abs().max().item())},
                      "path_tracing_1spp": out_pt}
         if prec == "fp16":
             # samples per ray and iteration (Fig. 13's K): the image does not depend on K

@@ -343,13 +343,16 @@ nv_status nv_render_rows(nv_renderer *r, nv_ctx *net, const nv_volume *raw, cons
                          int rows, float *rgba_dev);
 /* In-shader inference (Sec. 5.1, App. A): the same ray march as nv_render on
  * the network `net`, as one kernel in which each thread owns a ray and the
- * network is evaluated inside the march -- a CTA of 128 rays gathers one
- * sample per live ray into a tensor-core tile per iteration and runs until
- * its last ray finishes.  Samples, network arithmetic and compositing are
- * those of nv_render, so both give the same image; opts->K is ignored.  Needs
- * an FP16 or BF16 network of a tensor-core shape (NV_ERR_UNSUPPORTED
- * otherwise).  samples_dev (nullable): one int64 on the device, set to the
- * number of evaluated samples.  Asynchronous on the network's stream. */
+ * network is evaluated inside the march -- a CTA of 128 rays (a 16 x 8 pixel
+ * tile) gathers one sample per live ray into a tensor-core tile per iteration
+ * and runs until its last ray finishes.  Samples, network arithmetic and
+ * compositing are those of nv_render, so both give the same image; opts->K is
+ * ignored.  The fixed step only (opts->step_max > 0: NV_ERR_UNSUPPORTED);
+ * opts->shade == 1 adds nv_render's single-shot shadows, the shadow march run
+ * by the same thread after its ray's primary march.  Needs an FP16 or BF16
+ * network of a tensor-core shape (NV_ERR_UNSUPPORTED otherwise).  samples_dev
+ * (nullable): one int64 on the device, set to the number of evaluated samples
+ * (primary and shadow).  Asynchronous on the network's stream. */
 nv_status nv_render_inshader(nv_ctx *net, const nv_camera *cam, const float *lut_dev, const nv_macrocells *mc,
                              const nv_render_opts *opts, float *rgba_dev, int64_t *samples_dev);
 /* Volumetric path tracing with sample streaming (Sec. 5.2.2, Alg. 1, Eq. 1-2):

@@ -46,11 +46,13 @@ struct IsPlan {
   static constexpr int TOTAL = BAR + 16;
 };
 
-template <int D0, int F, bool BF>
+// SH: single-shot shadows compiled in (the emission-absorption kernel keeps
+// none of their state)
+template <int D0, int F, bool BF, bool SH>
 __global__ void __launch_bounds__(kTP, 7) k_render_is(NetDesc nd, const float *__restrict__ params,
                                                    const uint16_t *__restrict__ shadow, nv_camera cam, McView mc,
                                                    const float *__restrict__ lut, float step, float alpha_exp,
-                                                   float et, float4 *__restrict__ rgba,
+                                                   float et, ShadeArgs sh, float4 *__restrict__ rgba,
                                                    unsigned long long *samples, int *err) {
   using P = IsPlan<D0>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -108,7 +110,31 @@ __global__ void __launch_bounds__(kTP, 7) k_render_is(NetDesc nd, const float *_
   }
   float cr = 0.f, cg = 0.f, cb = 0.f, ca = 0.f;
   int k = 0;
-  McCache cache;
+  McCache cache;  // cells and their mu_max are the same for the primary and the shadow march
+  // single-shot shadows (Sec. 5): the largest contribution (1 - A) a' so far and
+  // its position; as < 0 during the primary march, then the shadow march's opacity
+  float bw = 0.f, bp[3] = {0.f, 0.f, 0.f}, as = -1.f;
+  // the primary march has ended: march on towards the light from the sample of
+  // largest contribution (same sampling rules, opacity only) if there is one
+  auto start_shadow = [&]() -> bool {
+    float s0, s1;
+    if (!(SH && bw > 0.f && nv_box(bp, sh.light, s0, s1))) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      o[a] = bp[a];
+      d[a] = sh.light[a];
+    }
+    t0 = s0;
+    t1 = s1;
+    k = 0;
+    as = 0.f;
+    return true;
+  };
+  auto finish = [&]() {
+    if (SH && as >= 0.f) shade_colour(sh, as, cr, cg, cb);  // shaded at the point of largest contribution
+    rgba[pix] = make_float4(cr, cg, cb, ca);
+    live = false;
+  };
   unsigned nsamp = 0;
   uint32_t phase = 0;
   bool failed = false;
@@ -123,14 +149,13 @@ __global__ void __launch_bounds__(kTP, 7) k_render_is(NetDesc nd, const float *_
   for (;;) {
     // ---- next sample of the ray (A-12) ----
     float pos[3] = {0.f, 0.f, 0.f};
-    if (live) {
+    while (live) {
       int m;
       while ((m = march_step(o, d, t0, t1, step, mc, k, pos, &cache)) == kMarchSkip) {
       }
-      if (m == kMarchEnd) {
-        live = false;  // left the volume
-        rgba[pix] = make_float4(cr, cg, cb, ca);
-      }
+      if (m != kMarchEnd) break;
+      // left the volume: the primary march may hand over to the shadow march
+      if (!(as < 0.f && start_shadow())) finish();
     }
     if (!__syncthreads_or(live)) break;
     // ---- its features, row `tid` of the tile (A-1..A-3; zero for idle rows) ----
@@ -204,11 +229,23 @@ __global__ void __launch_bounds__(kTP, 7) k_render_is(NetDesc nd, const float *_
     // ---- A-14: composite; a ray that reaches et is done ----
     if (live) {
       ++nsamp;
-      if (composite_one(yv, lut, alpha_exp, et, cr, cg, cb, ca)) {
-        live = false;
-        rgba[pix] = make_float4(cr, cg, cb, ca);
+      bool stop;
+      if (as < 0.f) {
+        float w;
+        stop = composite_one(yv, lut, alpha_exp, et, cr, cg, cb, ca, &w);
+        if (SH && w > bw) {
+          bw = w;
+          bp[0] = pos[0];
+          bp[1] = pos[1];
+          bp[2] = pos[2];
+        }
+      } else if constexpr (SH) {
+        stop = shadow_one(yv, lut, alpha_exp, et, as);
+      } else {
+        stop = false;  // no shadow march without SH (as stays < 0)
       }
       ++k;
+      if (stop && !(as < 0.f && start_shadow())) finish();
     }
   }
 
@@ -237,16 +274,17 @@ nv_status launch_is(nv_ctx *c, const nv_camera &cam, const float *lut, const McV
   size_t bytes = P::TOTAL + 1024;
   const size_t min_bytes = 233472 / (tmem_cap + 1) + 1024;
   if (bytes < min_bytes) bytes = min_bytes;
-  auto kern = k_render_is<D0, F, BF>;
+  auto kern = o.shade ? k_render_is<D0, F, BF, true> : k_render_is<D0, F, BF, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(k_render_is)");
   e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return nv_cuda_check(e, "cudaFuncSetAttribute(carveout)");
   const int64_t tiles_x = (cam.width + kIsTW - 1) / kIsTW, tiles_y = (cam.height + kTP / kIsTW - 1) / (kTP / kIsTW);
   const unsigned grid = (unsigned)(tiles_x * tiles_y);
+  const ShadeArgs sh{o.shade, {o.light[0], o.light[1], o.light[2]}, o.ambient};
   kern<<<grid, kTP, bytes, c->stream>>>(c->nd, c->params, reinterpret_cast<const uint16_t *>(c->shadow), cam, mv,
-                                        lut, o.step, o.alpha_exp, o.et, reinterpret_cast<float4 *>(rgba), samples,
-                                        &c->ds->err);
+                                        lut, o.step, o.alpha_exp, o.et, sh, reinterpret_cast<float4 *>(rgba),
+                                        samples, &c->ds->err);
   return nv_cuda_check(cudaGetLastError(), "k_render_is launch");
 }
 

@@ -406,10 +406,7 @@ __global__ void k_composite(const float *__restrict__ ray, const int *__restrict
     } else {  // the shadow march: opacity only
       for (int j = 0; j < nv; ++j) {
         const float ex = seg_exp ? seg_exp[i * K + j] : alpha_exp;
-        float r, g, b, ac;
-        tf_lookup(values[i * K + j], lut, ex, r, g, b, ac);
-        as += (1.0f - as) * ac;
-        if (as >= et) {
+        if (shadow_one(values[i * K + j], lut, ex, et, as)) {
           done = true;
           break;
         }
@@ -417,12 +414,7 @@ __global__ void k_composite(const float *__restrict__ ray, const int *__restrict
       if (nv < K) done = true;
     }
     if (done) {
-      if (as >= 0.f) {  // shaded at the point of largest contribution
-        const float k = sh.ambient + (1.0f - sh.ambient) * (1.0f - as);
-        cr *= k;
-        cg *= k;
-        cb *= k;
-      }
+      if (as >= 0.f) shade_colour(sh, as, cr, cg, cb);  // shaded at the point of largest contribution
       rgba[__float_as_int(ray[R_PIX * cap + i])] = make_float4(cr, cg, cb, ca);
     }
     live = !done;

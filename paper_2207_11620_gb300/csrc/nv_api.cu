@@ -693,8 +693,13 @@ extern "C" nv_status nv_render_inshader(nv_ctx *net, const nv_camera *cam, const
     return nv_fail(NV_ERR_ARG, "nv_render_inshader: step, alpha_exp and et must be > 0");
   if (mc && (!mc->mu_max_dev || mc->cell < 1 || mc->nx < 1 || mc->ny < 1 || mc->nz < 1))
     return nv_fail(NV_ERR_ARG, "nv_render_inshader: bad macrocell grid");
-  if (opts->step_max > 0.f || opts->shade != 0)
-    return nv_fail(NV_ERR_UNSUPPORTED, "nv_render_inshader: emission-absorption with the fixed step only");
+  if (opts->step_max > 0.f) return nv_fail(NV_ERR_UNSUPPORTED, "nv_render_inshader: the fixed step only");
+  if (opts->shade != 0 && opts->shade != 1) return nv_fail(NV_ERR_ARG, "nv_render_inshader: shade=%d", opts->shade);
+  if (opts->shade == 1) {
+    const float l2 = opts->light[0] * opts->light[0] + opts->light[1] * opts->light[1] + opts->light[2] * opts->light[2];
+    if (!(fabsf(l2 - 1.f) < 1e-3f) || !(opts->ambient >= 0.f && opts->ambient <= 1.f))
+      return nv_fail(NV_ERR_ARG, "nv_render_inshader: shadows need a unit light direction and ambient in [0, 1]");
+  }
   if (!(cam->tan_half_fovy >= 0.f)) return nv_fail(NV_ERR_ARG, "nv_render_inshader: tan_half_fovy < 0");
   return render_inshader(net, *cam, lut, mc, *opts, rgba, reinterpret_cast<unsigned long long *>(samples_dev));
 }

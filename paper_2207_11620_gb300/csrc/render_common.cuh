@@ -177,3 +177,22 @@ struct ShadeArgs {
   float light[3];  // unit direction towards the directional light
   float ambient;   // colour scale where the light is fully blocked
 };
+
+// One sample of the shadow march (opacity only): as += (1 - as) a', every
+// operation rounded on its own so the streaming and in-shader marches agree
+// bit for bit; returns whether the march stops (as >= et).
+__device__ __forceinline__ bool shadow_one(float v, const float *__restrict__ lut, float alpha_exp, float et,
+                                           float &as) {
+  float r, g, b, ac;
+  tf_lookup(v, lut, alpha_exp, r, g, b, ac);
+  as = __fadd_rn(as, __fmul_rn(__fsub_rn(1.0f, as), ac));
+  return as >= et;
+}
+
+// The colour of a shaded ray: C (ambient + (1 - ambient) T), T = 1 - as.
+__device__ __forceinline__ void shade_colour(const ShadeArgs &sh, float as, float &cr, float &cg, float &cb) {
+  const float k = __fadd_rn(sh.ambient, __fmul_rn(__fsub_rn(1.0f, sh.ambient), __fsub_rn(1.0f, as)));
+  cr = __fmul_rn(cr, k);
+  cg = __fmul_rn(cg, k);
+  cb = __fmul_rn(cb, k);
+}

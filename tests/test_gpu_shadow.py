@@ -116,3 +116,59 @@ def test_shadow_rejects_bad_light(nv):
     r = nv.Renderer(64, K=8)
     with pytest.raises(nv.NvError, match="unit light"):
         r.render(I.ortho_camera_z(8, 8), lt, dict(step=1 / 64, shade=1, light=(0.0, 2.0, 0.0)), raw=vt)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_inshader_shadows_equal_streaming_and_match_oracle(nv, prec):
+    """Single-shot shadows in the in-shader megakernel: the thread that ends a
+    primary march runs its shadow march, with the samples, values and
+    compositing of nv_render's, so the images agree; and against the oracle's
+    march of the same parameters on sampled pixels (the 16-bit network's
+    tolerance)."""
+    c = CF.CFG2_NET
+    net = nv.NeuralVolume(prec=prec, **c.kwargs())
+    params = I.init_params(net.n_table, net.n_params - net.n_table, seed=7, dims=c.dims)
+    params[: net.n_table] = I.uniform_params(net.n_table, seed=8, scale=0.5)
+    net.set_params(params)
+    vol = I.blob_volume((40, 48, 56), seed=5)
+    lut = I.ramp_lut_soft(0.1)
+    lt = torch.from_numpy(lut).cuda()
+    _, mu = nv.macrocells_build(torch.from_numpy(vol).cuda(), 8, lt)
+    mc = (mu, 8, vol.shape)
+    opts = dict(step=0.5 / 56, alpha_exp=0.5, et=0.99, K=8, mc_cell=8, shade=1, light=(0.48, 0.6, -0.64),
+                ambient=0.25)
+    cam = I.perspective_camera(70, 37)  # ragged 16 x 8 tiles
+    r = nv.Renderer(70 * 37, K=8)
+    ss = r.render(cam, lt, opts, net=net, mc=mc)
+    sam = torch.zeros(1, dtype=torch.int64, device="cuda")
+    is_ = nv.render_inshader(net, cam, lt, opts, mc=mc, samples=sam)
+    torch.cuda.synchronize()
+    assert (is_ - ss).abs().max().item() <= 1e-6
+    _, ns = r.stats()
+    # primary and shadow samples alike; the streaming march also evaluates the rest of
+    # its last batch of K samples past the opacity threshold
+    assert 0 < sam.item() <= ns
+    ea = nv.render_inshader(net, cam, lt, dict(opts, shade=0), mc=mc).cpu().numpy().reshape(-1, 4)
+    img = is_.cpu().numpy().reshape(-1, 4)
+    assert np.all(img[:, :3] <= ea[:, :3] + 1e-6)
+    assert (img[:, :3] < ea[:, :3] * 0.9).any()  # some light is blocked
+    np.testing.assert_array_equal(img[:, 3], ea[:, 3])  # shadows leave the opacity as it is
+    pix = np.random.default_rng(3).choice(70 * 37, 200, replace=False)
+    want = O.render_pixels(cam, lut, opts, pix, net=onet(c), params=params, vol=vol, mumax=mu.cpu().numpy())
+    diff = np.abs(img[pix] - want)
+    assert diff[:, 3].max() <= 5e-2
+    # a near tie for the largest contribution, which 16-bit values can break the other way, moves a
+    # pixel's shadow: such pixels must be rare
+    assert (diff[:, :3].max(axis=1) <= 5e-2).mean() >= 0.95
+
+
+def test_inshader_rejects_adaptive_step(nv):
+    c = CF.CFG1_NET
+    net = nv.NeuralVolume(prec="fp16", **c.kwargs())
+    net.set_params(I.uniform_params(net.n_params, seed=1))
+    vt = torch.from_numpy(I.blob_volume(16, seed=1)).cuda()
+    lt = torch.from_numpy(I.ramp_lut()).cuda()
+    _, mu = nv.macrocells_build(vt, 8, lt)
+    with pytest.raises(nv.NvError, match="fixed step"):
+        nv.render_inshader(net, I.ortho_camera_z(8, 8), lt, dict(step=1 / 64, step_max=4 / 64),
+                           mc=(mu, 8, (16, 16, 16)))
