@@ -7,11 +7,11 @@
 // few large CTAs, could not.  The adjoint scatter (A-7) runs inside the MLP
 // kernel's backward epilogue (k_tc.cu).
 //
-// Work item = (point, chunk of 8 features): with F features per level a chunk
-// covers 8 / F levels.  The grid's y index is the chunk and its x index runs
-// over points, so neighbouring threads handle neighbouring points at the same
-// levels (coarse-level table lines are shared in L1) and write one 16-byte
-// core-matrix row each.
+// Work item = (point, group of chunks of 8 features): with F features per
+// level a chunk covers 8 / F levels.  The grid's y index is the group and its
+// x index runs over points, so neighbouring threads handle neighbouring points
+// at the same levels (coarse-level table lines are shared in L1) and write
+// one 16-byte core-matrix row per chunk.
 #include "nv_internal.cuh"
 #include "tc_grid.cuh"
 
@@ -28,10 +28,9 @@ template <bool CORNERS>
 constexpr int kChunksPerThread = CORNERS ? 4 : 1;
 
 template <int F, bool BF, bool CORNERS>
-__global__ void __launch_bounds__(256, CORNERS ? 6 : 5) k_encode_tiles(NetDesc nd, const uint16_t *__restrict__ shadow, PointSrc ps,
-                                                      ChunkSpan cs, uint8_t *__restrict__ feat,
-                                                      float *__restrict__ tgt, float *__restrict__ xyz_out,
-                                                      int *off_flag) {
+__global__ void __launch_bounds__(256, CORNERS ? 6 : 5)
+    k_encode_tiles(NetDesc nd, const uint16_t *__restrict__ shadow, PointSrc ps, ChunkSpan cs,
+                   uint8_t *__restrict__ feat, float *__restrict__ tgt, float *__restrict__ xyz_out, int *off_flag) {
   const int D0 = nd.dims[0];
   const int64_t n = chunk_count(cs);
   const int64_t npad = (cs.cap + 127) & ~int64_t(127);

@@ -18,9 +18,10 @@
 // between the kernels).  Inference takes up to kChunkInfer = 2^23 (512 MB):
 // a render iteration's samples then go through in one or two launches, and
 // the ramp and tail every launch of either kernel pays cost more, at
-// 2^19-point chunks, than the features' round trip through HBM.  The scatter's vector
-// reductions keep the load/store path busy while the CTA's other phases wait
-// on the tensor core, so the MLP and the scatter overlap inside one kernel.
+// 2^19-point chunks, than the features' round trip through HBM.  The
+// scatter's vector reductions keep the load/store path busy while the CTA's
+// other phases wait on the tensor core, so the MLP and the scatter overlap
+// inside one kernel.
 //
 // One CTA = 256 threads; a tile is 128 points.  Point r of the tile is TMEM
 // lane r and is shared by threads r and r + 128: each handles half of the 64
