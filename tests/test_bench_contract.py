@@ -98,3 +98,18 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_render_gather_roofline_counts_corner_bytes_and_issue_rate(bench):
+    ns, ms = 100_000_000, 8.0
+    l2 = {"l1_gather_loads_per_s": 7e11, "gather_loads_per_s": 3e11}
+    r = bench.gather_roofline(ns, ms, 16, 2, 32, PK, "measured", l2)
+    assert r["algorithmic_bytes_per_frame"] == ns * 8 * 16 * 2 * 2  # 8 corners x L levels x F x 2 B
+    assert r["frac"] == pytest.approx(r["achieved"] / (7e11 * 16 / 1e9))
+    assert r["issued_corner_loads"]["per_frame"] == ns * 16 * 8
+    assert r["hbm"]["bytes_per_sample"] == 12 + 2 * 32
+    iss = r["issue"]  # warp instructions against one per SM sub-partition and cycle
+    ipl = bench.RENDER_GATHER_INSTR_PER_SAMPLE_LEVEL
+    assert iss["achieved_per_s"] == pytest.approx(ipl * ns * 16 / 32 / (ms / 1e3))
+    assert iss["frac"] == pytest.approx(iss["achieved_per_s"] / iss["peak_per_s"])
+    assert iss["peak_per_s"] % (4 * 2000e6) == 0  # 4 per SM per cycle at the maximum clock
